@@ -1,0 +1,361 @@
+"""Benchmark: reproducible PBiCGStab iterations per second on one GB300.
+
+Workload (one step = one full solve): 3D Poisson 7-point on a 256^3 grid
+(n = 16,777,216, nnz = 117,047,296), CSR binary64, b = A*1, x0 = 0, Jacobi,
+classic reproducible PBiCGStab (Fig. 2) with exact dots, stop at relative
+residual 1e-10. Inputs are synthetic (seeded generator) and resident in HBM
+when the timed region starts; the 1.8 GB matrix is larger than the 129 MB L2,
+so no flush is needed between steps.
+
+The JSON line also carries: `e2e` (the same solve through the C ABI from pinned
+host buffers, copies inside the timed region), `roofline` for the dominant
+kernel (SpMV + dot epilogue, CUDA events inside the library over the timed
+steps), `cpu_baseline` (the CPU oracle on a bounded sample), the plain
+non-reproducible comparator and the pipelined variant on the same workload,
+and the standalone exact-dot and SpMV kernel throughputs.
+
+`--impl reference` times the CPU oracle (this method has no other reference
+implementation) on the same workload, a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRID = 256  # --grid changes it for profiling runs only; the headline is 256^3
+TOL = 1e-10
+MAXIT = 20000
+METRIC = "reproducible PBiCGStab iters/s"
+UNIT = "iters/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload_config(A):
+    return {"workload": f"poisson3d_7pt_{GRID}^3 classic reproducible PBiCGStab, Jacobi, "
+                        f"b=A*1, x0=0, tol={TOL:g}",
+            "n": int(A.n), "nnz": int(A.nnz), "grid": GRID, "variant": "classic",
+            "tol": TOL, "dots": "exact, rounded once",
+            "l2": "inputs larger than L2 (1.8 GB CSR + vectors), no flush"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+        else:
+            self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_baseline(A, b, iters=2):
+    import oracle
+    oracle.build()
+    t = time.perf_counter()
+    o = oracle.solve(A, b, tol=TOL, maxit=iters, variant=0, history=False)
+    dt = time.perf_counter() - t
+    return {"value": o["iters"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"set-up + {o['iters']} classic iterations of the same 256^3 solve, "
+                      f"single-threaded C oracle ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if world > 1 and rank != 0:
+        return 0
+    from paper_2302_04180_gb300 import gen
+    import oracle
+    oracle.build()
+    A = gen.poisson3d(GRID)
+    b = oracle.spmv(A, np.ones(A.n))
+    per = 1
+    for _ in range(args.warmup):
+        oracle.solve(A, b, tol=TOL, maxit=per, variant=0, history=False)
+    t = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        its += oracle.solve(A, b, tol=TOL, maxit=per, variant=0, history=False)["iters"]
+    dt = time.perf_counter() - t
+    v = its / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _workload_config(A),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: set-up + {per} classic iteration of the "
+                                       "256^3 solve, single-threaded C oracle"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2302_04180_gb300 as rbs
+    from paper_2302_04180_gb300 import gen
+
+    A = gen.poisson3d(GRID)
+    Ad = rbs.to_device(A, dev)
+    ones = torch.ones(A.n, dtype=torch.float64, device=dev)
+    b = rbs.rbs_spmv_csr(Ad, ones)
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve(variant=0, dot_mode=0, profile=False, history=False):
+        return rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=variant, x_out=x,
+                             dot_mode=dot_mode, profile=profile, history=history)
+
+    for _ in range(args.warmup):
+        r0 = solve()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    prof_tot = {}
+    iters = 0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = solve(profile=True)
+            iters += r["iters"]
+            for k, (nl, ms) in r["prof"].items():
+                a = prof_tot.setdefault(k, [0, 0.0])
+                a[0] += nl
+                a[1] += ms
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return 0
+    value = world * iters / (ms * 1e-3)
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel: SpMV with its dot epilogue (classic K1, K3)
+    hbm, peak_kind = _peaks()
+    nl, kms = prof_tot.get("spmv_dot", [0, 0.0])
+    per_launch_ms = kms / max(nl, 1)
+    alg_bytes = 12 * A.nnz + 32 * A.n + 8
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if nl else None
+    shares = {k: round(v[1] / max(sum(t[1] for t in prof_tot.values()), 1e-12), 4)
+              for k, v in prof_tot.items()}
+    traffic = _traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                "kernel": "SpMV + exact-dot epilogue (classic K1/K3)",
+                "alg_bytes_per_launch": alg_bytes, "launches": nl,
+                "avg_launch_us": per_launch_ms * 1e3, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "time_share": shares}
+
+    if not args.extras:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": _workload_config(A), "clocks": clocks,
+                "roofline": roofline, "gpu_launches": sum(v[0] for v in prof_tot.values())}
+        print(json.dumps(line), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # e2e: the same solve through the C ABI from pinned host buffers
+    rp = torch.from_numpy(A.rowptr).pin_memory()
+    cl = torch.from_numpy(A.col).pin_memory()
+    vl = torch.from_numpy(A.val).pin_memory()
+    bh = b.cpu().pin_memory()
+    xh = torch.empty(A.n, dtype=torch.float64).pin_memory()
+    Ah = rbs.DeviceCSR(A.n, rp, cl, vl)
+    rbs.rbs_solve(Ah, bh, tol=TOL, maxit=MAXIT, variant=0, x_out=xh, history=False)
+    e2e_steps = max(1, min(args.steps, 3))
+    t = time.perf_counter()
+    e_iters = 0
+    for _ in range(e2e_steps):
+        e_iters += rbs.rbs_solve(Ah, bh, tol=TOL, maxit=MAXIT, variant=0, x_out=xh, history=False)["iters"]
+    e_dt = time.perf_counter() - t
+    h2d = 8 * (A.n + 1) + 4 * A.nnz + 8 * A.nnz + 8 * A.n
+    e2e = {"value": world * e_iters / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 8 * A.n + 4, "path": "rbs_solve on pinned host buffers"}
+
+    # comparators on the same workload (one solve each)
+    def once(**kw):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rr = solve(**kw)
+        torch.cuda.synchronize()
+        return rr, time.perf_counter() - t0
+
+    rp_, tp_ = once(dot_mode=1)
+    rq_, tq_ = once(variant=1)
+    r2, t2 = once()
+    plain = {"value": rp_["iters"] / tp_, "iters": rp_["iters"], "converged": rp_["converged"],
+             "what": "same loop, binary64 dots with atomic accumulation (non-reproducible)"}
+    repro_one = r2["iters"] / t2
+    pipelined = {"value": rq_["iters"] / tq_, "iters": rq_["iters"], "converged": rq_["converged"]}
+
+    kernels = _kernel_micro(rbs, gen, dev)
+    gpu_launches = sum(v[0] for v in prof_tot.values())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**_workload_config(A), "iters_per_solve": r["iters"],
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+            "plain_comparator": {**plain, "repro_over_plain_time": plain["value"] / repro_one},
+            "pipelined": pipelined, "kernels": kernels}
+    if args.cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(A, b.cpu().numpy())
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary (None when absent or stale)."""
+    p = os.path.join(ROOT, "profiles", "traffic_spmv_dot_poisson256.json")
+    try:
+        with open(p) as f:
+            return json.load(f).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def _kernel_micro(rbs, gen, dev):
+    """Standalone exact dot (2^27, cond 1e32) and SpMV (Poisson 128^3) GB/s."""
+    import torch
+    out = {}
+
+    def timeit(f, reps=10):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    n = 1 << 27
+    x, y, _ = gen.ill_conditioned_dot(n, 1e32, 0)
+    xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+    del x, y
+    o = torch.empty(1, dtype=torch.float64, device=dev)
+    ms = timeit(lambda: rbs.rbs_exdot(xt, yt, o))
+    out["exdot_2^27_cond1e32"] = {"us": ms * 1e3, "GB/s": 16 * n / (ms * 1e-3) / 1e9}
+    del xt, yt
+    A = gen.poisson3d(128)
+    Ad = rbs.to_device(A, dev)
+    xv = torch.from_numpy(gen.random_vector(A.n, 1)).to(dev)
+    yv = torch.empty_like(xv)
+    ms = timeit(lambda: rbs.rbs_spmv_csr(Ad, xv, yv))
+    byt = 12 * A.nnz + 8 * (A.n + 1) + 16 * A.n
+    out["spmv_poisson128"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--grid", type=int, default=256,
+                    help="Poisson grid side (profiling runs on smaller cases; the metric is 256)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip e2e, comparators and kernel microbenchmarks")
+    args = ap.parse_args()
+    global GRID
+    GRID = args.grid
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * rbs.h - C ABI of the GB300 (sm_103a) reproducible PBiCGStab library.
+ *
+ * Method: Iakymchuk & Aliaga, "General framework for re-assuring numerical
+ * reliability in parallel Krylov solvers: A case of BiCGStab methods"
+ * (arXiv 2302.04180). The library computes the data-parallel hot path of the
+ * paper's reproducible and accurate preconditioned BiCGStab (Fig. 2) and
+ * pipelined preconditioned BiCGStab (Fig. 4): the exact, correctly rounded dot
+ * product (Sec. 2, Sec. 3.2), the fma-ordered CSR SpMV and the Jacobi and
+ * axpy-like updates (Sec. 3.3, Sec. 4.1), and the scalar recurrences of both
+ * loops. All arithmetic is IEEE-754 binary64, round to nearest even, plus exact
+ * integer accumulation; every result is bitwise independent of the launch
+ * configuration and of scheduling.
+ *
+ * Conventions for every entry point:
+ *  - Pointers are plain C pointers. Unless an argument says otherwise it must
+ *    point to device memory of the current CUDA device; arguments marked
+ *    "host or device" may point to either (the library asks the CUDA runtime
+ *    which one it is and stages host data through its own device buffers).
+ *  - Vectors are contiguous binary64 arrays, 8-byte aligned; 16-byte alignment
+ *    enables the vectorised load path (results are identical either way).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Work is
+ *    enqueued on it in order. Calls that return results in host memory
+ *    synchronise the stream before returning.
+ *  - The caller owns every buffer it passes and keeps it alive until the
+ *    stream has finished the call. The library owns a per-(device, stream)
+ *    workspace that it creates on first use and frees in rbs_release().
+ *  - Errors are returned as an int status (RBS_OK = 0); no C++ exception
+ *    crosses the ABI. rbs_last_error() gives a one-line message for the
+ *    calling thread's last failure.
+ *  - Kernels never read out of bounds: every CSR index is checked on the
+ *    device before use. A bad index is skipped and recorded in the
+ *    workspace's error word; synchronising calls then return RBS_EINVAL, and
+ *    asynchronous calls report it through rbs_stream_status().
+ */
+#ifndef RBS_H
+#define RBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define RBS_OK 0
+#define RBS_EINVAL 1      /* bad argument: null pointer, n < 0, invalid CSR, zero or missing diagonal */
+#define RBS_ENOMEM 2      /* device or pinned host allocation failed */
+#define RBS_ECUDA 3       /* a CUDA runtime call failed (message in rbs_last_error) */
+#define RBS_EBREAKDOWN 4  /* a zero denominator stopped the solver (history so far is kept) */
+#define RBS_ENAN 5        /* a non-finite scalar stopped the solver */
+#define RBS_ETIMEOUT 6    /* a bounded device-side wait expired */
+
+/* ---- sparse matrix ----------------------------------------------------------
+ * CSR, n x n: rowptr[n+1] (int64, rowptr[0] = 0, non-decreasing,
+ * rowptr[n] = nnz), col[nnz] (int32, 0 <= col < n), val[nnz] (binary64). The
+ * stored order of each row is the order of its fma chain and is never changed;
+ * duplicate column entries are allowed and kept. Device pointers (rbs_solve
+ * also accepts host pointers). */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *rowptr;
+    const int32_t *col;
+    const double *val;
+} rbs_csr;
+
+/* ---- exact dot product (Sec. 2 "ExBLAS ... exdot"; Sec. 3.2) ------------------
+ * out = RN(sum_{i<n} x[i]*y[i]): every product is formed exactly (53x53-bit
+ * integer significands), accumulated exactly in a Kulisch-style fixed-point
+ * accumulator covering 2^-2148 .. 2^2200, and rounded once to nearest even.
+ * An exact zero gives +0.0; n == 0 gives +0.0. A NaN operand, an inf*0 product
+ * or infinite products of both signs give NaN; otherwise an infinite product
+ * gives that infinity; finite products are always summed exactly, and an exact
+ * sum beyond the binary64 range rounds to +-inf.
+ * x, y: n binary64 (host or device). out: 1 binary64 (host or device; host
+ * output synchronises the stream). Asynchronous with device output. */
+int rbs_exdot(const double *x, const double *y, int64_t n, double *out, void *stream);
+
+/* k exact dots over the same length in one pass (Sec. 4.1: S10 and S11 merged
+ * in one reduction; Sec. 4.2: the two- and four-dot reductions of Fig. 4).
+ * xs[j], ys[j] (j < k, 1 <= k <= 6): host arrays of device pointers; operands may
+ * repeat (e.g. <r0,r> and <r,r>). out: k binary64 (host or device). */
+int rbs_exdot_multi(int k, const double *const *xs, const double *const *ys, int64_t n,
+                    double *out, void *stream);
+
+/* Long-accumulator export for row-block ranks (Sec. 3.2): a rank's exact
+ * partial sum of x[i]*y[i] as RBS_LIMBS int64 limbs, limb j weighing
+ * 2^(32j - 2148), plus a flags word (bit 0: NaN, bit 1: +inf product,
+ * bit 2: -inf product). Limb values are signed and partially normalised
+ * (|limb| < 2^34), so ranks may add limb arrays as plain integers, in any
+ * order, up to 2^28 of them, OR the flags, and round once with
+ * rbs_round_limbs: the result is bitwise the single-rank rbs_exdot.
+ * limbs: RBS_LIMBS int64 (device); flags: 1 int32 (device). */
+#define RBS_LIMBS 136
+int rbs_exdot_partial(const double *x, const double *y, int64_t n, int64_t *limbs,
+                      int32_t *flags, void *stream);
+/* out = RN(value of the limb array) (host or device out; device limbs). */
+int rbs_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, void *stream);
+
+/* ---- fma-ordered SpMV (Sec. 4.1 "Sparse matrix-vector product"; Sec. 3.3) ----
+ * y[i] = fma(val[last], x[col[last]], ... fma(val[first], x[col[first]], +0.0))
+ * over row i in stored order, every step rounded to nearest even; an empty row
+ * gives +0.0. x: A->n binary64, y: A->n binary64 (device; y must not alias x).
+ * Asynchronous. */
+int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream);
+
+/* ---- Jacobi preconditioner (Sec. 4: M = diag(A), applied element-wise) ------
+ * invd[i] = RN(1 / d[i]) with d = diag (if non-null) else the first stored
+ * entry (i, i) of row i. Synchronises; RBS_EINVAL on a zero, NaN or missing
+ * diagonal. invd: n binary64 (device). */
+int rbs_jacobi_invd(const rbs_csr *A, const double *diag, double *invd, void *stream);
+/* phat[i] = RN(p[i] * invd[i]). Asynchronous. */
+int rbs_jacobi_apply(int64_t n, const double *invd, const double *p, double *phat,
+                     void *stream);
+
+/* ---- solver ------------------------------------------------------------------ */
+#define RBS_CLASSIC 0   /* PBiCGStab, Fig. 2 */
+#define RBS_PIPELINED 1 /* p-PBiCGStab, Fig. 4 */
+
+#define RBS_DOT_EXACT 0 /* reproducible: exact dots rounded once (the method) */
+#define RBS_DOT_PLAIN 1 /* comparator: binary64 dots with atomic accumulation,
+                           run-to-run non-reproducible (the paper's "original") */
+
+#define RBS_LOOP_GRAPH 0 /* the loop runs on the device: one iteration is the body of a
+                            CUDA-graph conditional WHILE node (no host round trips) */
+#define RBS_LOOP_HOST 1  /* the host enqueues iterations in chunks and reads the stop flag */
+
+typedef struct {
+    int32_t dot_mode;    /* RBS_DOT_EXACT (default) or RBS_DOT_PLAIN */
+    int32_t check_every; /* RBS_LOOP_HOST: iterations enqueued between host reads of the
+                            stop flag; 0 = library default */
+    int32_t profile;     /* 1: time every kernel launch with CUDA events, see rbs_prof
+                            (uses RBS_LOOP_HOST) */
+    int32_t loop_mode;   /* RBS_LOOP_GRAPH (default) or RBS_LOOP_HOST. Results do not
+                            depend on loop_mode or check_every. */
+} rbs_opts;
+
+typedef struct {
+    int32_t iters;     /* loop bodies executed */
+    int32_t converged; /* 1 iff tau <= tau_max at exit and status == RBS_OK */
+    int32_t status;    /* RBS_OK, RBS_EBREAKDOWN or RBS_ENAN (also the return value) */
+    int32_t reserved;
+    double tau0;       /* RN(sqrt(<r0, r0>)) */
+    double tau_final;  /* tau of the last iteration (tau0 if none) */
+    double rho0;       /* <r0, r0> */
+    double tau_max;    /* RN(tol * tau0) */
+    double alpha0;     /* pipelined: RN(<r0,r0> / <r0,w0>) (NaN if not computed) */
+    double mu0;        /* pipelined: <r0, w0> */
+} rbs_info;
+
+/* Per-iteration record of every scalar, RBS_HIST_W binary64 each; fields not
+ * computed in an iteration hold the quiet NaN 0x7ff8000000000000.
+ *  classic:   0 sigma=<r0,s> 1 alpha 2 gamma=<q,y> 3 delta=<y,y> 4 omega
+ *             5 rho'=<r0,r> 6 theta=<r,r> 7 tau 8 beta
+ *  pipelined: 0 gamma=<q,y> 1 delta=<y,y> 2 omega 3 rho'=<r0,r> 4 <r0,w>
+ *             5 <r0,s> 6 <r0,z> 7 theta=<r,r> 8 tau 9 beta 10 alpha denominator
+ *             11 next alpha
+ * rec: host array of cap * RBS_HIST_W binary64; len receives the number of
+ * records written (= iters, at most cap). */
+#define RBS_HIST_W 12
+typedef struct {
+    int32_t cap;
+    int32_t len;
+    double *rec;
+} rbs_history;
+
+/* Kernel timing from rbs_opts.profile: per kernel kind, launches and summed
+ * CUDA-event milliseconds over the whole solve. */
+#define RBS_PROF_KINDS 8
+typedef struct {
+    int64_t launches[RBS_PROF_KINDS];
+    double ms[RBS_PROF_KINDS];
+    /* kinds: 0 SpMV (+dot epilogue), 1 vector update (+dots), 2 set-up,
+       3 standalone SpMV (pipelined S10/S18), 4..7 unused */
+} rbs_prof;
+
+/* Solve A x = b with Jacobi-preconditioned BiCGStab (Fig. 2) or pipelined
+ * BiCGStab (Fig. 4), with reproducible exact dots, stopping when
+ * tau = RN(sqrt(<r,r>)) <= RN(tol * tau0) or after maxit iterations.
+ * Readings of the figures (all bitwise-pinned against the CPU oracle):
+ *  r0 = RN(b - A x0) element-wise (x0 NULL: zero and r0 = b); invd = RN(1/d);
+ *  x-update fma(omega, qhat, fma(alpha, phat, x)); classic p-update
+ *  fma(beta, fma(-omega, s, p), r); beta = RN(RN(rho'/rho) * RN(alpha/omega));
+ *  pipelined alpha denominator fma(-RN(beta*omega), <r0,z>, fma(beta, <r0,s>, <r0,w>));
+ *  pipelined tau from a fifth dot <r,r> in the S16 reduction; pipelined
+ *  iteration 0 starts from copies (beta = 0); <y,y> == 0 gives omega = 0; the
+ *  stop test runs as soon as tau is known; zero denominators stop with
+ *  RBS_EBREAKDOWN; non-finite scalars stop with RBS_ENAN.
+ * A, b, x0, jacobi_diag: host or device. x_out: n binary64, host or device.
+ * info (host, required), hist (host, nullable), prof (host, nullable),
+ * opts (host, nullable = defaults). Synchronises the stream. */
+int rbs_solve(const rbs_csr *A, const double *b, const double *x0, const double *jacobi_diag,
+              double tol, int32_t maxit, int32_t variant, double *x_out, rbs_info *info,
+              rbs_history *hist, void *stream);
+int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0,
+                 const double *jacobi_diag, double tol, int32_t maxit, int32_t variant,
+                 const rbs_opts *opts, double *x_out, rbs_info *info, rbs_history *hist,
+                 rbs_prof *prof, void *stream);
+
+/* ---- library control ---------------------------------------------------------- */
+/* Synchronise `stream`, then return and clear the workspace error word:
+ * RBS_OK, or RBS_EINVAL if a kernel met an out-of-range CSR index. */
+int rbs_stream_status(void *stream);
+/* Free every workspace of the calling process (all devices and streams). */
+int rbs_release(void);
+/* Launch-shape knobs for tuning and for configuration-independence tests.
+ * Names: "exdot.grid", "exdot.block", "exdot.window" (0 = auto),
+ * "spmv.block", "vec.grid", "vec.block". Results never depend on them. */
+int rbs_set_param(const char *name, int64_t value);
+int64_t rbs_get_param(const char *name);
+const char *rbs_last_error(void);
+const char *rbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBS_H */

@@ -1,0 +1,651 @@
+// C ABI of the library (declared in include/rbs.h): argument checks, the
+// per-(device, stream) workspace, host/device staging, and the solver driver
+// that enqueues iterations and watches the device-resident stop flag.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace rbs {
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? RBS_ENOMEM : RBS_ECUDA;
+}
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ---- knobs -------------------------------------------------------------------------
+std::atomic<int64_t> p_exdot_grid{0}, p_exdot_block{0}, p_exdot_window{0}, p_spmv_block{0},
+    p_vec_grid{0}, p_vec_block{0}, p_check_every{0};
+
+std::atomic<int64_t> *param_slot(const char *name) {
+    if (!name) return nullptr;
+    if (!strcmp(name, "exdot.grid")) return &p_exdot_grid;
+    if (!strcmp(name, "exdot.block")) return &p_exdot_block;
+    if (!strcmp(name, "exdot.window")) return &p_exdot_window;
+    if (!strcmp(name, "spmv.block")) return &p_spmv_block;
+    if (!strcmp(name, "vec.grid")) return &p_vec_grid;
+    if (!strcmp(name, "vec.block")) return &p_vec_block;
+    if (!strcmp(name, "solve.check_every")) return &p_check_every;
+    return nullptr;
+}
+
+int block_of(int64_t v, int def) {
+    if (v <= 0) return def;
+    int b = (int)(v > 256 ? 256 : v);
+    b = (b / 32) * 32;
+    return b < 32 ? 32 : b;
+}
+
+// ---- workspace ----------------------------------------------------------------------
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+cudaError_t ensure(Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.cap = bytes;
+    return e;
+}
+
+constexpr int NVEC = 18;
+constexpr int NFLAGS = 64;
+
+struct Workspace {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    DotScratch *g = nullptr;
+    SolverState *st = nullptr;
+    SolverState *h_st = nullptr;
+    int32_t *h_flags = nullptr;
+    double *h_out = nullptr;
+    double *d_out = nullptr;
+    unsigned *h_err = nullptr;
+    Buf vec, hist, stage[8];
+    std::vector<cudaEvent_t> evpool;
+    std::vector<cudaEvent_t> ev_chunk;
+    // graph loop: one iteration captured as the body of a conditional WHILE node
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string graph_key;
+    std::mutex mu;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace *> g_ws;
+
+int ws_get(cudaStream_t s, Workspace **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(dev, s);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) {
+        *out = it->second;
+        return RBS_OK;
+    }
+    Workspace *w = new Workspace();
+    w->dev = dev;
+    w->stream = s;
+    cudaError_t e = cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaMalloc(&w->g, sizeof(DotScratch));
+    if (e == cudaSuccess) e = cudaMemset(w->g, 0, sizeof(DotScratch));
+    if (e == cudaSuccess) e = cudaMalloc(&w->st, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaMalloc(&w->d_out, KMAX * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&w->h_st, sizeof(SolverState));
+    if (e == cudaSuccess) e = cudaMallocHost(&w->h_flags, NFLAGS * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&w->h_out, KMAX * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&w->h_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        delete w;
+        return cuda_fail(e, "workspace creation");
+    }
+    g_ws[key] = w;
+    *out = w;
+    return RBS_OK;
+}
+
+void ws_free(Workspace *w) {
+    cudaSetDevice(w->dev);
+    if (w->stream) cudaStreamSynchronize(w->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(w->g);
+    cudaFree(w->st);
+    cudaFree(w->d_out);
+    cudaFreeHost(w->h_st);
+    cudaFreeHost(w->h_flags);
+    cudaFreeHost(w->h_out);
+    cudaFreeHost(w->h_err);
+    cudaFree(w->vec.p);
+    cudaFree(w->hist.p);
+    for (auto &b : w->stage) cudaFree(b.p);
+    for (auto e : w->evpool) cudaEventDestroy(e);
+    for (auto e : w->ev_chunk) cudaEventDestroy(e);
+    if (w->exec) cudaGraphExecDestroy(w->exec);
+    if (w->graph) cudaGraphDestroy(w->graph);
+    if (w->cap) cudaStreamDestroy(w->cap);
+    delete w;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// device view of a caller buffer: the pointer itself, or a staged copy
+int to_device(Workspace *w, int slot, const void *p, size_t bytes, const void **out) {
+    if (!p || bytes == 0 || is_device_ptr(p)) {
+        *out = p;
+        return RBS_OK;
+    }
+    CK(ensure(w->stage[slot], bytes));
+    CK(cudaMemcpyAsync(w->stage[slot].p, p, bytes, cudaMemcpyHostToDevice, w->stream));
+    *out = w->stage[slot].p;
+    return RBS_OK;
+}
+
+int read_err(Workspace *w, unsigned *err) {
+    CK(cudaMemcpyAsync(w->h_err, &w->g->err, sizeof(unsigned), cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaMemsetAsync(&w->g->err, 0, sizeof(unsigned), w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    *err = *w->h_err;
+    return RBS_OK;
+}
+
+Cfg grid_for(Workspace *w, int64_t items, int block, int per_sm) {
+    Cfg c;
+    c.block = block;
+    int64_t need = (items + block - 1) / block;
+    int64_t cap = (int64_t)w->sms * per_sm;
+    c.grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
+    return c;
+}
+
+// Exact-dot launch shape: persistent grid, and never more than 2^20 products
+// per thread per launch (the register window's headroom).
+Cfg exdot_cfg(Workspace *w, int64_t n) {
+    Cfg c;
+    c.block = block_of(p_exdot_block.load(), 256);
+    int64_t g = p_exdot_grid.load();
+    if (g <= 0) {
+        int64_t need = (n + 2LL * c.block - 1) / (2LL * c.block);
+        int64_t cap = (int64_t)w->sms * 4;
+        g = need < 1 ? 1 : (need < cap ? need : cap);
+    }
+    int64_t minimum = (n + ((int64_t)c.block << 20) - 1) / ((int64_t)c.block << 20);
+    if (g < minimum) g = minimum;
+    if (g > 0x7fffffff) g = 0x7fffffff;
+    c.grid = (int)g;
+    return c;
+}
+
+int window_param() {
+    int64_t q = p_exdot_window.load();
+    return (q == 1 || q == 2 || q == 4) ? (int)q : 4;
+}
+
+struct EventTimer : KernelTimer {
+    Workspace *w;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> rec;
+    size_t used = 0;
+    cudaError_t err = cudaSuccess;
+    explicit EventTimer(Workspace *ws) : w(ws) {}
+    cudaEvent_t take() {
+        if (used == w->evpool.size()) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) {
+                err = r;
+                return nullptr;
+            }
+            w->evpool.push_back(e);
+        }
+        return w->evpool[used++];
+    }
+    void before(int kind) override {
+        cudaEvent_t a = take();
+        if (!a) return;
+        cudaEventRecord(a, w->stream);
+        rec.push_back({kind, {a, nullptr}});
+    }
+    void after(int kind) override {
+        (void)kind;
+        cudaEvent_t b = take();
+        if (!b || rec.empty()) return;
+        cudaEventRecord(b, w->stream);
+        rec.back().second.second = b;
+    }
+};
+
+// Build (or reuse) the executable graph whose WHILE node replays one solver
+// iteration until the device stop flag is set. Kernel arguments are baked in,
+// so the graph is keyed by every launch argument; device scalars (tol, maxit)
+// are not arguments and may change between solves.
+int graph_loop(Workspace *w, const SolverArgs &a, int variant) {
+    std::string key((const char *)&a, sizeof a);
+    key.append((const char *)&variant, sizeof variant);
+    if (!(w->exec && key == w->graph_key)) {
+        if (w->exec) cudaGraphExecDestroy(w->exec);
+        if (w->graph) cudaGraphDestroy(w->graph);
+        w->exec = nullptr;
+        w->graph = nullptr;
+        w->graph_key.clear();
+        if (!w->cap) CK(cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        CK(cudaGraphCreate(&g, 0));
+        w->graph = g;
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        CK(cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e1 = solver_iteration(a, variant, w->cap, nullptr);
+        cudaError_t e2 = launch_set_cond(h, a.st, w->cap);
+        cudaGraph_t out = nullptr;
+        cudaError_t e3 = cudaStreamEndCapture(w->cap, &out);
+        if (e1 != cudaSuccess) return cuda_fail(e1, "capture of the iteration");
+        if (e2 != cudaSuccess) return cuda_fail(e2, "capture of the loop condition");
+        if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamEndCapture");
+        cudaGraphExec_t ex;
+        CK(cudaGraphInstantiate(&ex, g, 0));
+        w->exec = ex;
+        w->graph_key = key;
+    }
+    CK(cudaGraphLaunch(w->exec, w->stream));
+    return RBS_OK;
+}
+
+}  // namespace
+}  // namespace rbs
+
+using namespace rbs;
+
+extern "C" {
+
+const char *rbs_version(void) { return "rbs 0.1 (sm_103a)"; }
+
+const char *rbs_last_error(void) { return g_err.c_str(); }
+
+int rbs_set_param(const char *name, int64_t value) {
+    auto *s = param_slot(name);
+    if (!s) return fail(RBS_EINVAL, std::string("unknown parameter ") + (name ? name : "(null)"));
+    s->store(value);
+    return RBS_OK;
+}
+
+int64_t rbs_get_param(const char *name) {
+    auto *s = param_slot(name);
+    return s ? s->load() : -1;
+}
+
+int rbs_release(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev0 = 0;
+    cudaGetDevice(&dev0);
+    for (auto &kv : g_ws) ws_free(kv.second);
+    g_ws.clear();
+    cudaSetDevice(dev0);
+    return RBS_OK;
+}
+
+int rbs_stream_status(void *stream) {
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    unsigned err = 0;
+    rc = read_err(w, &err);
+    if (rc) return rc;
+    if (err) return fail(RBS_EINVAL, "a kernel met an out-of-range CSR index");
+    return RBS_OK;
+}
+
+static int exdot_common(int k, const double *const *xs, const double *const *ys, int64_t n, double *out,
+                        void *stream) {
+    if (k < 1 || k > KMAX) return fail(RBS_EINVAL, "k must be in 1..6");
+    if (n < 0) return fail(RBS_EINVAL, "n < 0");
+    if (!out || !xs || !ys) return fail(RBS_EINVAL, "null pointer");
+    for (int j = 0; j < k; j++)
+        if (n > 0 && (!xs[j] || !ys[j])) return fail(RBS_EINVAL, "null operand");
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    const bool out_dev = is_device_ptr(out);
+    double *dout = out_dev ? out : w->d_out;
+    if (n == 0) {
+        if (out_dev) {
+            CK(cudaMemsetAsync(out, 0, k * sizeof(double), w->stream));
+        } else {
+            for (int j = 0; j < k; j++) out[j] = 0.0;
+        }
+        return RBS_OK;
+    }
+    const double *dx[KMAX], *dy[KMAX];
+    for (int j = 0; j < k; j++) {
+        const void *p;
+        if ((rc = to_device(w, 2 * j % 8, xs[j], (size_t)n * 8, &p))) return rc;
+        dx[j] = (const double *)p;
+        if ((rc = to_device(w, (2 * j + 1) % 8, ys[j], (size_t)n * 8, &p))) return rc;
+        dy[j] = (const double *)p;
+    }
+    CK(launch_exdot(k, dx, dy, n, w->g, dout, window_param(), exdot_cfg(w, n), w->stream));
+    if (!out_dev) {
+        CK(cudaMemcpyAsync(w->h_out, w->d_out, k * sizeof(double), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+        for (int j = 0; j < k; j++) out[j] = w->h_out[j];
+    }
+    return RBS_OK;
+}
+
+int rbs_exdot(const double *x, const double *y, int64_t n, double *out, void *stream) {
+    const double *xs[1] = {x}, *ys[1] = {y};
+    return exdot_common(1, xs, ys, n, out, stream);
+}
+
+int rbs_exdot_multi(int k, const double *const *xs, const double *const *ys, int64_t n, double *out,
+                    void *stream) {
+    if (k >= 1 && k <= KMAX && xs && ys)
+        for (int j = 0; j < k; j++)
+            if (n > 0 && (!is_device_ptr(xs[j]) || !is_device_ptr(ys[j])))
+                return fail(RBS_EINVAL, "rbs_exdot_multi operands must be device pointers");
+    return exdot_common(k, xs, ys, n, out, stream);
+}
+
+int rbs_exdot_partial(const double *x, const double *y, int64_t n, int64_t *limbs, int32_t *flags,
+                      void *stream) {
+    if (n < 0 || !limbs || !flags || (n > 0 && (!x || !y))) return fail(RBS_EINVAL, "bad argument");
+    if (!is_device_ptr(limbs) || !is_device_ptr(flags) || (n > 0 && (!is_device_ptr(x) || !is_device_ptr(y))))
+        return fail(RBS_EINVAL, "rbs_exdot_partial takes device pointers");
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    if (n == 0) {
+        CK(cudaMemsetAsync(limbs, 0, RBS_LIMBS * sizeof(int64_t), w->stream));
+        CK(cudaMemsetAsync(flags, 0, sizeof(int32_t), w->stream));
+        return RBS_OK;
+    }
+    CK(launch_exdot_partial(x, y, n, w->g, limbs, flags, 4, exdot_cfg(w, n), w->stream));
+    return RBS_OK;
+}
+
+int rbs_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, void *stream) {
+    if (!limbs || !flags || !out) return fail(RBS_EINVAL, "null pointer");
+    if (!is_device_ptr(limbs) || !is_device_ptr(flags)) return fail(RBS_EINVAL, "limbs/flags must be device pointers");
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    const bool out_dev = is_device_ptr(out);
+    CK(launch_round_limbs(limbs, flags, out_dev ? out : w->d_out, w->stream));
+    if (!out_dev) {
+        CK(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+        *out = w->h_out[0];
+    }
+    return RBS_OK;
+}
+
+static int check_csr_args(const rbs_csr *A) {
+    if (!A) return fail(RBS_EINVAL, "A is null");
+    if (A->n <= 0 || A->n > 0x7fffffff) return fail(RBS_EINVAL, "A->n must be in 1..2^31-1");
+    if (A->nnz < 0) return fail(RBS_EINVAL, "A->nnz < 0");
+    if (!A->rowptr || (A->nnz > 0 && (!A->col || !A->val))) return fail(RBS_EINVAL, "null CSR array");
+    return RBS_OK;
+}
+
+int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream) {
+    int rc = check_csr_args(A);
+    if (rc) return rc;
+    if (!x || !y) return fail(RBS_EINVAL, "null vector");
+    if (x == y) return fail(RBS_EINVAL, "y must not alias x");
+    Workspace *w;
+    if ((rc = ws_get((cudaStream_t)stream, &w))) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    CSRArgs a{A->n, A->nnz, A->rowptr, A->col, A->val};
+    Cfg c = grid_for(w, A->n, block_of(p_spmv_block.load(), 256), 8);
+    CK(launch_spmv(a, x, y, nullptr, &w->g->err, c, w->stream));
+    return RBS_OK;
+}
+
+int rbs_jacobi_invd(const rbs_csr *A, const double *diag, double *invd, void *stream) {
+    int rc = check_csr_args(A);
+    if (rc) return rc;
+    if (!invd) return fail(RBS_EINVAL, "null invd");
+    Workspace *w;
+    if ((rc = ws_get((cudaStream_t)stream, &w))) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    CSRArgs a{A->n, A->nnz, A->rowptr, A->col, A->val};
+    Cfg c = grid_for(w, A->n, 256, 8);
+    CK(launch_jacobi_invd(a, diag, invd, &w->g->err, c, w->stream));
+    unsigned err = 0;
+    if ((rc = read_err(w, &err))) return rc;
+    if (err & 2u) return fail(RBS_EINVAL, "zero, NaN or missing diagonal entry");
+    if (err) return fail(RBS_EINVAL, "invalid CSR row pointers");
+    return RBS_OK;
+}
+
+int rbs_jacobi_apply(int64_t n, const double *invd, const double *p, double *phat, void *stream) {
+    if (n < 0 || (n > 0 && (!invd || !p || !phat))) return fail(RBS_EINVAL, "bad argument");
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    if (n == 0) return RBS_OK;
+    CK(launch_jacobi_apply(n, invd, p, phat, grid_for(w, n, 256, 8), w->stream));
+    return RBS_OK;
+}
+
+int rbs_solve(const rbs_csr *A, const double *b, const double *x0, const double *jacobi_diag, double tol,
+              int32_t maxit, int32_t variant, double *x_out, rbs_info *info, rbs_history *hist,
+              void *stream) {
+    return rbs_solve_ex(A, b, x0, jacobi_diag, tol, maxit, variant, nullptr, x_out, info, hist, nullptr,
+                        stream);
+}
+
+int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const double *jacobi_diag,
+                 double tol, int32_t maxit, int32_t variant, const rbs_opts *opts, double *x_out,
+                 rbs_info *info, rbs_history *hist, rbs_prof *prof, void *stream) {
+    if (info) memset(info, 0, sizeof *info);
+    if (info) info->status = RBS_EINVAL;
+    int rc = check_csr_args(A);
+    if (rc) return rc;
+    if (!b || !x_out || !info) return fail(RBS_EINVAL, "null b, x_out or info");
+    if (maxit < 0 || !(tol >= 0.0)) return fail(RBS_EINVAL, "maxit < 0 or tol not >= 0");
+    if (variant != RBS_CLASSIC && variant != RBS_PIPELINED) return fail(RBS_EINVAL, "unknown variant");
+    if (hist && (hist->cap < 0 || (hist->cap > 0 && !hist->rec))) return fail(RBS_EINVAL, "bad history");
+    rbs_opts o{};
+    if (opts) o = *opts;
+    if (o.dot_mode != RBS_DOT_EXACT && o.dot_mode != RBS_DOT_PLAIN) return fail(RBS_EINVAL, "bad dot_mode");
+    if (o.loop_mode != RBS_LOOP_GRAPH && o.loop_mode != RBS_LOOP_HOST) return fail(RBS_EINVAL, "bad loop_mode");
+    if (prof) memset(prof, 0, sizeof *prof);
+
+    Workspace *w;
+    if ((rc = ws_get((cudaStream_t)stream, &w))) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    const int64_t n = A->n, nnz = A->nnz;
+
+    // caller buffers, staged to the device when they live in host memory
+    const void *rowptr, *col, *val, *db, *dx0 = nullptr, *ddiag = nullptr;
+    if ((rc = to_device(w, 0, A->rowptr, (size_t)(n + 1) * 8, &rowptr))) return rc;
+    if ((rc = to_device(w, 1, A->col, (size_t)nnz * 4, &col))) return rc;
+    if ((rc = to_device(w, 2, A->val, (size_t)nnz * 8, &val))) return rc;
+    if ((rc = to_device(w, 3, b, (size_t)n * 8, &db))) return rc;
+    if (x0 && (rc = to_device(w, 4, x0, (size_t)n * 8, &dx0))) return rc;
+    if (jacobi_diag && (rc = to_device(w, 5, jacobi_diag, (size_t)n * 8, &ddiag))) return rc;
+
+    // solver vectors, 256-byte aligned each
+    const size_t stride = ((size_t)n * 8 + 255) / 256 * 256;
+    CK(ensure(w->vec, stride * NVEC));
+    double *vp[NVEC];
+    for (int i = 0; i < NVEC; i++) vp[i] = (double *)((char *)w->vec.p + stride * i);
+    const bool xout_dev = is_device_ptr(x_out) && ((uintptr_t)x_out % 16 == 0);
+    SolverVecs V;
+    V.x = xout_dev ? x_out : vp[0];
+    V.r = vp[1]; V.r0 = vp[2]; V.p = vp[3]; V.ph = vp[4]; V.s = vp[5]; V.q = vp[6]; V.qh = vp[7];
+    V.y = vp[8]; V.invd = vp[9]; V.rh = vp[10]; V.w = vp[11]; V.wh = vp[12]; V.t = vp[13];
+    V.sh = vp[14]; V.z = vp[15]; V.zh = vp[16]; V.v = vp[17];
+
+    const int hcap = hist ? (hist->cap < maxit ? hist->cap : maxit) : 0;
+    CK(ensure(w->hist, (size_t)(hcap > 0 ? hcap : 1) * RBS_HIST_W * 8));
+
+    SolverState *h = w->h_st;
+    memset(h, 0, sizeof *h);
+    h->tol = tol;
+    h->maxit = maxit;
+    h->variant = variant;
+    h->hist_cap = hcap;
+    CK(cudaMemcpyAsync(w->st, h, sizeof *h, cudaMemcpyHostToDevice, w->stream));
+    CK(cudaMemsetAsync(&w->g->err, 0, sizeof(unsigned), w->stream));
+
+    SolverArgs a;
+    memset(&a, 0, sizeof a);  // padding too: the struct keys the graph cache
+    a.A = CSRArgs{n, nnz, (const int64_t *)rowptr, (const int32_t *)col, (const double *)val};
+    a.v = V;
+    a.b = (const double *)db;
+    a.x0 = (const double *)dx0;
+    a.st = w->st;
+    a.g = w->g;
+    a.hist = (double *)w->hist.p;
+    a.err = &w->g->err;
+    a.dot_mode = o.dot_mode;
+    {
+        const int vb = block_of(p_vec_block.load(), 256);
+        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1);
+        a.vec = grid_for(w, (n + 1) / 2, vb, bps);
+        if (p_vec_grid.load() > 0) a.vec.grid = (int)p_vec_grid.load();
+        const int sb = block_of(p_spmv_block.load(), 256);
+        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0));
+        // window headroom: at most 2^20 products per thread per launch
+        const int64_t minv = (n + ((int64_t)a.vec.block << 20) - 1) / ((int64_t)a.vec.block << 20);
+        if (a.vec.grid < minv) a.vec.grid = (int)minv;
+        const int64_t mins = (n + ((int64_t)a.spmv.block << 20) - 1) / ((int64_t)a.spmv.block << 20);
+        if (a.spmv.grid < mins) a.spmv.grid = (int)mins;
+    }
+
+    // structure check and Jacobi set-up (Sec. 4: M = diag(A))
+    CK(launch_csr_check(a.A, &w->g->err, grid_for(w, nnz > n ? nnz : n, 256, 8), w->stream));
+    CK(launch_jacobi_invd(a.A, (const double *)ddiag, V.invd, &w->g->err, grid_for(w, n, 256, 8), w->stream));
+    unsigned err = 0;
+    if ((rc = read_err(w, &err))) return rc;
+    if (err & 1u) return fail(RBS_EINVAL, "invalid CSR structure");
+    if (err & 2u) return fail(RBS_EINVAL, "zero, NaN or missing diagonal entry");
+
+    EventTimer timer(w);
+    KernelTimer *tm = (o.profile && prof) ? &timer : nullptr;
+    CK(solver_setup(a, variant, w->stream, tm));
+
+    const bool use_graph = !tm && o.loop_mode == RBS_LOOP_GRAPH && maxit > 0;
+    if (use_graph) {
+        if ((rc = graph_loop(w, a, variant))) return rc;
+    }
+    int chunk = o.check_every > 0 ? o.check_every : (p_check_every.load() > 0 ? (int)p_check_every.load() : 8);
+    if (!use_graph && w->ev_chunk.size() < 2) {
+        for (int i = (int)w->ev_chunk.size(); i < 2; i++) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            w->ev_chunk.push_back(e);
+        }
+    }
+    // keep one chunk of iterations enqueued ahead of the flag being read
+    int64_t launched = 0;
+    int slot = 0, prev = -1;
+    while (!use_graph) {
+        int cur = -1;
+        if (launched < maxit) {
+            int m = (int)((maxit - launched) < chunk ? (maxit - launched) : chunk);
+            for (int i = 0; i < m; i++) CK(solver_iteration(a, variant, w->stream, tm));
+            launched += m;
+            cur = slot;
+            CK(cudaMemcpyAsync(&w->h_flags[cur], &w->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               w->stream));
+            CK(cudaEventRecord(w->ev_chunk[cur], w->stream));
+            slot ^= 1;
+        }
+        if (prev >= 0) {
+            CK(cudaEventSynchronize(w->ev_chunk[prev]));
+            if (w->h_flags[prev]) break;
+        }
+        if (cur < 0) break;
+        prev = cur;
+    }
+    CK(cudaMemcpyAsync(h, w->st, sizeof *h, cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    if ((rc = read_err(w, &err))) return rc;
+    if (err) return fail(RBS_EINVAL, "a kernel met an out-of-range CSR index");
+
+    info->iters = h->iter;
+    info->status = h->status;
+    info->tau0 = h->tau0;
+    info->tau_final = h->tau;
+    info->rho0 = h->rho0;
+    info->tau_max = h->tau_max;
+    info->alpha0 = variant == RBS_PIPELINED ? h->alpha0 : __builtin_nan("");
+    info->mu0 = variant == RBS_PIPELINED ? h->mu0 : 0.0;
+    info->converged = (h->status == RBS_OK && !(h->tau > h->tau_max)) ? 1 : 0;
+    if (hist) {
+        hist->len = h->iter < hcap ? h->iter : hcap;
+        if (hist->len > 0)
+            CK(cudaMemcpyAsync(hist->rec, w->hist.p, (size_t)hist->len * RBS_HIST_W * 8,
+                               cudaMemcpyDeviceToHost, w->stream));
+    }
+    if (!xout_dev)
+        CK(cudaMemcpyAsync(x_out, V.x, (size_t)n * 8,
+                           is_device_ptr(x_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    if (tm) {
+        for (auto &r : timer.rec) {
+            if (!r.second.second) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess &&
+                r.first < RBS_PROF_KINDS) {
+                prof->ms[r.first] += ms;
+                prof->launches[r.first] += 1;
+            }
+        }
+    }
+    if (h->status != RBS_OK)
+        return fail(h->status, h->status == RBS_EBREAKDOWN ? "breakdown: zero denominator"
+                                                           : "non-finite scalar");
+    return RBS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,328 @@
+// Exact dot-product accumulation on sm_103a (Sec. 2 "ExBLAS"; Sec. 3.2).
+//
+// The paper's exdot keeps every bit of every product (TwoProd, Alg. 2) in
+// floating-point expansions and a Kulisch long accumulator, and rounds once.
+// On GB300 the binary64 pipe issues under two operations per SM per clock, so
+// this design keeps the exact work off it entirely:
+//
+//  * each product x*y is formed exactly as a 106-bit integer (four 32x32->64
+//    integer multiply-adds on the 53-bit significands) at bit position
+//    pos = e_x + e_y - 2, the accumulator's bit 0 weighing 2^-2148 (the lowest
+//    bit of a product of two subnormals). This is TwoProd's exact r + s, in
+//    integer form, with no underflow or overflow exception;
+//  * each thread adds its products into a 256-bit two's complement register
+//    window anchored at a 32-bit limb `a`; a product lands at limb offset
+//    q = (pos >> 5) - a in [0, Q) with a funnel shift and a log-shifter of
+//    word selects, then one 8-word add with carry;
+//  * products above the window flush it and re-anchor it; products below it
+//    are added straight into the block's shared-memory long accumulator
+//    (RBS_LIMBS signed 64-bit limbs, limb j weighing 2^(32 j - 2148), carry-save
+//    with 31 spare bits, the paper's "carry-safe bits" of Sec. 3.2);
+//  * at the end each window is added into the shared accumulator, the block
+//    accumulator is partially normalised and added into a global one with
+//    integer atomics (exact, so order does not matter), and the last block
+//    normalises, rounds once to nearest even and resets the scratch.
+//
+// The value is therefore the exact sum rounded once, whatever the grid, block
+// size, window size or schedule.
+#pragma once
+
+#include "common.cuh"
+
+namespace rbs {
+
+// ---- the register window ----------------------------------------------------
+
+// Anchor of an empty window: far below every limb, so that no product ever
+// matches the in-window test (q = L - a >= Q) and the first one anchors it.
+constexpr int WIN_EMPTY = -(1 << 30);
+
+template <int Q>
+struct Win {
+    uint32_t w[8];
+    int a;  // anchor limb, WIN_EMPTY when empty
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int k = 0; k < 8; k++) w[k] = 0u;
+        a = WIN_EMPTY;
+    }
+};
+
+// w += (v ^ m) + (m & 1) over 8 words: adds v, or subtracts it when m = ~0.
+__device__ __forceinline__ void add8_signed(uint32_t (&w)[8], const uint32_t (&v)[8], uint32_t m) {
+    uint32_t c = m & 1u;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %8, 0xffffffff;\n\t"
+        "addc.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.cc.u32 %2, %2, %11;\n\t"
+        "addc.cc.u32 %3, %3, %12;\n\t"
+        "addc.cc.u32 %4, %4, %13;\n\t"
+        "addc.cc.u32 %5, %5, %14;\n\t"
+        "addc.cc.u32 %6, %6, %15;\n\t"
+        "addc.u32 %7, %7, %16;\n\t}"
+        : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]),
+          "+r"(w[7])
+        : "r"(c), "r"(v[0] ^ m), "r"(v[1] ^ m), "r"(v[2] ^ m), "r"(v[3] ^ m), "r"(v[4] ^ m),
+          "r"(v[5] ^ m), "r"(v[6] ^ m), "r"(v[7] ^ m));
+}
+
+// The 106-bit product p (4 words) shifted left by r in [0, 31]: 5 words.
+__device__ __forceinline__ void shift5(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3, uint32_t r,
+                                       uint32_t (&u)[5]) {
+    u[0] = p0 << r;
+    u[1] = __funnelshift_l(p0, p1, r);
+    u[2] = __funnelshift_l(p1, p2, r);
+    u[3] = __funnelshift_l(p2, p3, r);
+    u[4] = __funnelshift_l(p3, 0u, r);
+}
+
+template <int Q>
+__device__ __forceinline__ void win_place_add(Win<Q> &W, const uint32_t (&u)[5], int q, uint32_t m) {
+    uint32_t v[8];
+    if (Q == 1) {
+        v[0] = u[0]; v[1] = u[1]; v[2] = u[2]; v[3] = u[3]; v[4] = u[4];
+        v[5] = 0u; v[6] = 0u; v[7] = 0u;
+    } else {
+        const bool b1 = (q & 1) != 0;
+        uint32_t t[6];
+        t[0] = b1 ? 0u : u[0];
+        t[1] = b1 ? u[0] : u[1];
+        t[2] = b1 ? u[1] : u[2];
+        t[3] = b1 ? u[2] : u[3];
+        t[4] = b1 ? u[3] : u[4];
+        t[5] = b1 ? u[4] : 0u;
+        if (Q == 2) {
+#pragma unroll
+            for (int k = 0; k < 6; k++) v[k] = t[k];
+            v[6] = 0u; v[7] = 0u;
+        } else {
+            const bool b2 = (q & 2) != 0;
+            v[0] = b2 ? 0u : t[0];
+            v[1] = b2 ? 0u : t[1];
+            v[2] = b2 ? t[0] : t[2];
+            v[3] = b2 ? t[1] : t[3];
+            v[4] = b2 ? t[2] : t[4];
+            v[5] = b2 ? t[3] : t[5];
+            v[6] = b2 ? t[4] : 0u;
+            v[7] = b2 ? t[5] : 0u;
+        }
+    }
+    add8_signed(W.w, v, m);
+}
+
+// Add the window into the block accumulator as carry-save limbs: words 0..6
+// unsigned, word 7 the signed top of the two's complement value.
+template <int Q>
+__device__ __forceinline__ void win_flush(Win<Q> &W, unsigned long long *sacc) {
+    if (W.a < 0) return;
+#pragma unroll
+    for (int k = 0; k < 7; k++)
+        if (W.w[k]) atomicAdd(&sacc[W.a + k], (unsigned long long)W.w[k]);
+    if (W.w[7]) atomicAdd(&sacc[W.a + 7], (unsigned long long)(long long)(int32_t)W.w[7]);
+#pragma unroll
+    for (int k = 0; k < 8; k++) W.w[k] = 0u;
+    W.a = WIN_EMPTY;
+}
+
+// Product straight into the block accumulator (rare path).
+__device__ __forceinline__ void smem_deposit(unsigned long long *sacc, const uint32_t (&u)[5], int L,
+                                             uint32_t m) {
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        if (u[k]) {
+            unsigned long long v = (unsigned long long)u[k];
+            atomicAdd(&sacc[L + k], m ? (unsigned long long)(-(long long)v) : v);
+        }
+    }
+}
+
+// Non-finite operand handling (reading of the paper's silence; see rbs.h).
+static __device__ __noinline__ uint32_t special_flags(uint32_t xh, uint32_t xl, uint32_t yh, uint32_t yl) {
+    const uint32_t ex = (xh >> 20) & 0x7ffu, ey = (yh >> 20) & 0x7ffu;
+    const bool xnan = ex == 0x7ffu && ((xh & 0xfffffu) | xl) != 0u;
+    const bool ynan = ey == 0x7ffu && ((yh & 0xfffffu) | yl) != 0u;
+    if (xnan || ynan) return F_NAN;
+    const bool xzero = ((xh & 0x7fffffffu) | xl) == 0u;
+    const bool yzero = ((yh & 0x7fffffffu) | yl) == 0u;
+    if (xzero || yzero) return F_NAN;  // inf * 0
+    return ((xh ^ yh) & 0x80000000u) ? F_NINF : F_PINF;
+}
+
+// Exact accumulation of x*y into window W / block accumulator sacc.
+template <int Q>
+__device__ __forceinline__ void exact_add(Win<Q> &W, uint32_t &flags, unsigned long long *sacc, double x,
+                                          double y) {
+    const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+    const uint32_t yh = (uint32_t)__double2hiint(y), yl = (uint32_t)__double2loint(y);
+    const uint32_t ex = (xh >> 20) & 0x7ffu, ey = (yh >> 20) & 0x7ffu;
+    if (ex == 0x7ffu || ey == 0x7ffu) {
+        flags |= special_flags(xh, xl, yh, yl);
+        return;
+    }
+    const uint32_t A1 = (xh & 0xfffffu) | (ex ? 0x100000u : 0u);
+    const uint32_t B1 = (yh & 0xfffffu) | (ey ? 0x100000u : 0u);
+    if ((A1 | xl) == 0u || (B1 | yl) == 0u) return;  // a zero product adds nothing
+    const int pos = (int)max(ex, 1u) + (int)max(ey, 1u) - 2;
+    // 106-bit significand product (A1:xl) * (B1:yl)
+    const unsigned long long m00 = (unsigned long long)xl * yl;
+    const unsigned long long m01 = (unsigned long long)xl * B1 + (m00 >> 32);
+    const unsigned long long m10 = (unsigned long long)A1 * yl + (uint32_t)m01;
+    const unsigned long long m11 =
+        (unsigned long long)A1 * B1 + (unsigned long long)((uint32_t)(m01 >> 32) + (uint32_t)(m10 >> 32));
+    const uint32_t p0 = (uint32_t)m00, p1 = (uint32_t)m10, p2 = (uint32_t)m11, p3 = (uint32_t)(m11 >> 32);
+    const uint32_t m = (uint32_t)((int32_t)(xh ^ yh) >> 31);
+    const int L = pos >> 5;
+    uint32_t u[5];
+    shift5(p0, p1, p2, p3, (uint32_t)pos & 31u, u);
+    int q = L - W.a;
+    if ((unsigned)q < (unsigned)Q) {
+        win_place_add<Q>(W, u, q, m);
+        return;
+    }
+    if (W.a < 0 || q >= Q) {
+        // empty, or above the window: flush and re-anchor with the product at
+        // offset Q-2 (or 0), leaving room for somewhat larger products
+        win_flush<Q>(W, sacc);
+        int a = L - (Q >= 2 ? Q - 2 : 0);
+        a = a < 0 ? 0 : a;
+        W.a = a;
+        win_place_add<Q>(W, u, L - a, m);
+        return;
+    }
+    smem_deposit(sacc, u, L, m);
+}
+
+// ---- block- and grid-level reduction ------------------------------------------
+
+// Zero the block accumulators (K of them). All threads call it; ends in a barrier.
+template <int K>
+__device__ __forceinline__ void sacc_zero(unsigned long long (*sacc)[NL], uint32_t *sflags) {
+    for (int j = threadIdx.x; j < K * NL; j += blockDim.x) (&sacc[0][0])[j] = 0ull;
+    if (threadIdx.x < K) sflags[threadIdx.x] = 0u;
+    __syncthreads();
+}
+
+// Partially normalise a carry-save limb array value by value:
+// out_j = lo32(L_j) + (L_{j-1} >> 32); the top limb keeps its full value.
+__device__ __forceinline__ long long partial_norm(const unsigned long long *L, int j) {
+    const long long cur = (long long)L[j];
+    const long long below = j > 0 ? ((long long)L[j - 1] >> 32) : 0;
+    if (j == NL - 1) return cur + below;
+    return (long long)(cur & 0xffffffffll) + below;
+}
+
+// Round an exact value given as carry-save signed limbs (|limb| < 2^62) once
+// to nearest even. G is modified (normalised in place). One thread.
+static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t flags) {
+    if (flags & F_NAN) return qnan();
+    if ((flags & F_PINF) && (flags & F_NINF)) return qnan();
+    if (flags & F_PINF) return __longlong_as_double(0x7ff0000000000000ll);
+    if (flags & F_NINF) return __longlong_as_double((long long)0xfff0000000000000ull);
+    int lo = -1, hi = -1;
+    for (int j = 0; j < NL; j++)
+        if (G[j] != 0) {
+            if (lo < 0) lo = j;
+            hi = j;
+        }
+    if (lo < 0) return 0.0;
+    // carry propagation from lo up; two limbs past hi the carry is 0 or -1
+    int top = hi + 2 < NL - 1 ? hi + 2 : NL - 1;
+    long long c = 0;
+    for (int j = lo; j <= top; j++) {
+        const long long t = G[j] + c;
+        G[j] = t & 0xffffffffll;
+        c = t >> 32;
+    }
+    const bool neg = c < 0;
+    if (neg) {  // magnitude = two's complement negation of words lo..top
+        unsigned long long cy = 1;
+        for (int j = lo; j <= top; j++) {
+            const unsigned long long t = (unsigned long long)(~(uint32_t)G[j]) + cy;
+            G[j] = (long long)(t & 0xffffffffull);
+            cy = t >> 32;
+        }
+    }
+    int tw = -1;
+    for (int j = top; j >= lo; j--)
+        if (G[j] != 0) {
+            tw = j;
+            break;
+        }
+    if (tw < 0) return 0.0;
+    const int h = 32 * tw + 31 - __clz((uint32_t)G[tw]);  // top set bit
+    const int lsb = h - 52 > 1074 ? h - 52 : 1074;         // bit 1074 weighs 2^-1074
+    const int len = h - lsb + 1;
+    auto word = [&](int j) -> unsigned long long {
+        return (j >= lo && j <= top) ? (unsigned long long)(uint32_t)G[j] : 0ull;
+    };
+    const int w0 = lsb >> 5, s = lsb & 31;
+    const unsigned long long lo64 = word(w0) | (word(w0 + 1) << 32);
+    unsigned long long mant = lo64 >> s;
+    if (s) mant |= word(w0 + 2) << (64 - s);
+    mant &= (len >= 64) ? ~0ull : ((1ull << len) - 1ull);
+    int round_bit = 0, sticky = 0;
+    if (lsb >= 1) {
+        const int rb = lsb - 1;
+        round_bit = (int)((word(rb >> 5) >> (rb & 31)) & 1ull);
+        const int sw = rb >> 5, sb = rb & 31;
+        if (sb && (word(sw) & ((1ull << sb) - 1ull))) sticky = 1;
+        for (int j = lo; j < sw && !sticky; j++)
+            if (word(j)) sticky = 1;
+    }
+    if (round_bit && (sticky || (mant & 1ull))) mant += 1ull;
+    // value = mant * 2^(lsb - 2148); as binary64 bits: ((lsb - 1074) << 52) + mant
+    unsigned long long bits = ((unsigned long long)(lsb - 1074) << 52) + mant;
+    if (lsb - 1074 >= 2047 || bits >= 0x7ff0000000000000ull) bits = 0x7ff0000000000000ull;
+    if (neg) bits |= 0x8000000000000000ull;
+    return __longlong_as_double((long long)bits);
+}
+
+// Grid-level finish of K exact reductions. Every thread of every block calls it
+// after its last exact_add. Returns true in the block that finishes last; there
+// the rounded values are in vals[0..K-1] (shared memory) after a barrier.
+template <int K, int Q>
+__device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
+                                             unsigned long long (*sacc)[NL], uint32_t *sflags,
+                                             DotScratch *g, double *vals, bool export_limbs = false,
+                                             long long *limbs_out = nullptr, int32_t *flags_out = nullptr) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        win_flush<Q>(win[k], sacc[k]);
+        if (flags[k]) atomicOr(&sflags[k], flags[k]);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) {
+        const int k = idx / NL, j = idx - k * NL;
+        const long long v = partial_norm(sacc[k], j);
+        if (v) atomicAdd(&g->limbs[k][j], (unsigned long long)v);
+    }
+    if (threadIdx.x < K && sflags[threadIdx.x]) atomicOr(&g->flags[threadIdx.x], sflags[threadIdx.x]);
+    __threadfence();
+    __syncthreads();
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) s_last = (atomicAdd(&g->ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // read back (and clear) the global accumulators into shared memory
+    for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) {
+        const int k = idx / NL, j = idx - k * NL;
+        sacc[k][j] = atomicExch(&g->limbs[k][j], 0ull);
+    }
+    if (threadIdx.x < K) sflags[threadIdx.x] = atomicExch(&g->flags[threadIdx.x], 0u);
+    if (threadIdx.x == 0) g->ticket = 0u;
+    __syncthreads();
+    if (export_limbs) {
+        for (int idx = threadIdx.x; idx < NL; idx += blockDim.x)
+            limbs_out[idx] = partial_norm(sacc[0], idx);
+        if (threadIdx.x == 0) *flags_out = (int32_t)sflags[0];
+        return true;
+    }
+    if (threadIdx.x < K) vals[threadIdx.x] = round_limbs_thread((long long *)sacc[threadIdx.x], sflags[threadIdx.x]);
+    __syncthreads();
+    return true;
+}
+
+}  // namespace rbs

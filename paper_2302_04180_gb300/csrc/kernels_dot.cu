@@ -1,0 +1,213 @@
+// Standalone kernels: exact dot (single and multi-output), long-accumulator
+// export and rounding, fma-ordered SpMV, Jacobi, CSR validation.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace rbs {
+
+template <int K>
+struct DotArgs {
+    const double *x[K];
+    const double *y[K];
+};
+
+// K exact dots over the same length (Sec. 2 exdot; Sec. 4.1/4.2 merged
+// reductions). Aligned operands go through 16-byte loads, two pairs deep.
+template <int K, int Q, bool EXPORT>
+__global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool aligned, DotScratch *g,
+                                              double *out, long long *limbs, int32_t *flags_out) {
+    ExactR<K, Q> red;
+    red.init();
+    if (aligned) {
+        const int64_t n2 = n >> 1, st = gstride();
+        int64_t j = gtid();
+        for (; j + st < n2; j += 2 * st) {
+            double2 xa[K], ya[K], xb[K], yb[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                xa[k] = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + j);
+                ya[k] = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + j);
+                xb[k] = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + j + st);
+                yb[k] = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + j + st);
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                red.add(k, xa[k].x, ya[k].x);
+                red.add(k, xa[k].y, ya[k].y);
+                red.add(k, xb[k].x, yb[k].x);
+                red.add(k, xb[k].y, yb[k].y);
+            }
+        }
+        if (j < n2) {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const double2 xv = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + j);
+                const double2 yv = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + j);
+                red.add(k, xv.x, yv.x);
+                red.add(k, xv.y, yv.y);
+            }
+        }
+        if ((n & 1) && gtid() == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k++) red.add(k, a.x[k][n - 1], a.y[k][n - 1]);
+        }
+    } else {
+        for (int64_t i = gtid(); i < n; i += gstride()) {
+#pragma unroll
+            for (int k = 0; k < K; k++) red.add(k, a.x[k][i], a.y[k][i]);
+        }
+    }
+    __shared__ double vals[K];
+    if (EXPORT) {
+        exact_finish<K, Q>(red.win, red.flags, red.sacc, red.sflags, g, vals, true, limbs, flags_out);
+    } else {
+        if (red.finish(g, vals) && threadIdx.x < K) out[threadIdx.x] = vals[threadIdx.x];
+    }
+}
+
+template <int K, int Q>
+static cudaError_t exdot_k(const double *const *xs, const double *const *ys, int64_t n, DotScratch *g,
+                           double *out, Cfg cfg, cudaStream_t s) {
+    DotArgs<K> a;
+    bool aligned = true;
+    for (int k = 0; k < K; k++) {
+        a.x[k] = xs[k];
+        a.y[k] = ys[k];
+        aligned = aligned && ((uintptr_t)xs[k] % 16 == 0) && ((uintptr_t)ys[k] % 16 == 0);
+    }
+    k_exdot<K, Q, false><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, out, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+template <int Q>
+static cudaError_t exdot_q(int k, const double *const *xs, const double *const *ys, int64_t n,
+                           DotScratch *g, double *out, Cfg cfg, cudaStream_t s) {
+    switch (k) {
+        case 1: return exdot_k<1, Q>(xs, ys, n, g, out, cfg, s);
+        case 2: return exdot_k<2, Q>(xs, ys, n, g, out, cfg, s);
+        case 3: return exdot_k<3, Q>(xs, ys, n, g, out, cfg, s);
+        case 4: return exdot_k<4, Q>(xs, ys, n, g, out, cfg, s);
+        case 5: return exdot_k<5, Q>(xs, ys, n, g, out, cfg, s);
+        case 6: return exdot_k<6, Q>(xs, ys, n, g, out, cfg, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,
+                         DotScratch *g, double *out, int window, Cfg cfg, cudaStream_t s) {
+    if (window == 2) return exdot_q<2>(k, xs, ys, n, g, out, cfg, s);
+    if (window == 1) return exdot_q<1>(k, xs, ys, n, g, out, cfg, s);
+    return exdot_q<4>(k, xs, ys, n, g, out, cfg, s);
+}
+
+cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, DotScratch *g,
+                                 int64_t *limbs, int32_t *flags, int window, Cfg cfg, cudaStream_t s) {
+    (void)window;
+    DotArgs<1> a;
+    a.x[0] = x;
+    a.y[0] = y;
+    const bool aligned = ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0);
+    k_exdot<1, 4, true><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, nullptr, (long long *)limbs,
+                                                        flags);
+    return cudaGetLastError();
+}
+
+__global__ void k_round_limbs(const int64_t *limbs, const int32_t *flags, double *out) {
+    __shared__ long long G[NL];
+    for (int j = threadIdx.x; j < NL; j += blockDim.x) G[j] = (long long)limbs[j];
+    __syncthreads();
+    if (threadIdx.x == 0) *out = round_limbs_thread(G, (uint32_t)*flags);
+}
+
+cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, cudaStream_t s) {
+    k_round_limbs<<<1, 160, 0, s>>>(limbs, flags, out);
+    return cudaGetLastError();
+}
+
+// y = A x (Sec. 4.1), one thread per row, rows in a grid-stride loop. With a
+// solver state, the kernel is a no-op once the solver has stopped.
+__global__ void __launch_bounds__(256) k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y,
+                                              const SolverState *st, unsigned *err) {
+    if (st && st->done) return;
+    bool bad = false;
+    for (int64_t i = gtid(); i < A.n; i += gstride()) y[i] = spmv_row(A, i, x, bad);
+    if (bad) atomicOr(err, 1u);
+}
+
+static CSRView view(const CSRArgs &A) { return CSRView{A.n, A.nnz, A.rowptr, A.col, A.val}; }
+
+cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
+                        unsigned *err, Cfg cfg, cudaStream_t s) {
+    k_spmv<<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err);
+    return cudaGetLastError();
+}
+
+// invd_i = RN(1 / d_i) with d the given diagonal or the first stored (i, i)
+// entry (Sec. 4, Jacobi M = diag(A)); a zero, NaN or missing entry sets err bit 2.
+__global__ void __launch_bounds__(256) k_jacobi_invd(CSRView A, const double *diag, double *invd, unsigned *err) {
+    bool bad = false, idx_bad = false;
+    for (int64_t i = gtid(); i < A.n; i += gstride()) {
+        double d = 0.0;
+        bool found = false;
+        if (diag) {
+            d = diag[i];
+            found = true;
+        } else {
+            const int64_t b = A.rowptr[i], e = A.rowptr[i + 1];
+            if (b < 0 || e < b || e > A.nnz) {
+                idx_bad = true;
+            } else {
+                for (int64_t k = b; k < e; k++)
+                    if ((int64_t)A.col[k] == i) {
+                        d = A.val[k];
+                        found = true;
+                        break;
+                    }
+            }
+        }
+        if (!found || d == 0.0 || d != d) {
+            bad = true;
+            invd[i] = 0.0;
+        } else {
+            invd[i] = __ddiv_rn(1.0, d);
+        }
+    }
+    if (bad) atomicOr(err, 2u);
+    if (idx_bad) atomicOr(err, 1u);
+}
+
+cudaError_t launch_jacobi_invd(const CSRArgs &A, const double *diag, double *invd, unsigned *err, Cfg cfg,
+                               cudaStream_t s) {
+    k_jacobi_invd<<<cfg.grid, cfg.block, 0, s>>>(view(A), diag, invd, err);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_apply(int64_t n, const double *invd, const double *p,
+                                                     double *phat) {
+    for (int64_t i = gtid(); i < n; i += gstride()) phat[i] = __dmul_rn(p[i], invd[i]);
+}
+
+cudaError_t launch_jacobi_apply(int64_t n, const double *invd, const double *p, double *phat, Cfg cfg,
+                                cudaStream_t s) {
+    k_jacobi_apply<<<cfg.grid, cfg.block, 0, s>>>(n, invd, p, phat);
+    return cudaGetLastError();
+}
+
+// CSR structure check: rowptr[0] == 0, non-decreasing, rowptr[n] == nnz,
+// 0 <= col < n. Sets err bit 1 on any violation.
+__global__ void __launch_bounds__(256) k_csr_check(CSRView A, unsigned *err) {
+    bool bad = false;
+    if (gtid() == 0 && (A.rowptr[0] != 0 || A.rowptr[A.n] != A.nnz)) bad = true;
+    for (int64_t i = gtid(); i < A.n; i += gstride())
+        if (A.rowptr[i + 1] < A.rowptr[i]) bad = true;
+    for (int64_t k = gtid(); k < A.nnz; k += gstride())
+        if ((uint64_t)(int64_t)A.col[k] >= (uint64_t)A.n) bad = true;
+    if (bad) atomicOr(err, 1u);
+}
+
+cudaError_t launch_csr_check(const CSRArgs &A, unsigned *err, Cfg cfg, cudaStream_t s) {
+    k_csr_check<<<cfg.grid, cfg.block, 0, s>>>(view(A), err);
+    return cudaGetLastError();
+}
+
+}  // namespace rbs

@@ -1,0 +1,535 @@
+// Fused kernels of the classic (Fig. 2) and pipelined (Fig. 4) PBiCGStab
+// loops, with device-resident scalars. Every dot rides in the epilogue of the
+// kernel that produces its operands, and the block that finishes a reduction
+// last computes the scalar recurrence (alpha, omega, beta, tau, stop test) in
+// place, so the host never sits between two steps.
+//
+// Classic iteration (5 launches):
+//   K1  s = A phat, <r0,s>                      -> alpha          (S2, S3)
+//   K2  q = fma(-alpha, s, r), qhat = q*invd                        (S4, S5)
+//   K3  y = A qhat, <q,y>, <y,y>                -> omega          (S6, S7)
+//   K4  x = fma(omega, qhat, fma(alpha, phat, x)), r = fma(-omega, y, q),
+//       <r0,r>, <r,r>                           -> tau, stop, beta (S8-S11, S10)
+//   K5  p = fma(beta, fma(-omega, s, p), r), phat = p*invd        (S12, S1)
+// Pipelined iteration (4 launches):
+//   P1  S1-S7 and S9 element-wise, <q,y>, <y,y>  -> omega          (S1-S9, S11)
+//   P2  v = A zhat                                                  (S10)
+//   P3  S12-S15 and S17 element-wise, <r0,r>, <r0,w>, <r0,s>, <r0,z>, <r,r>
+//                                                -> tau, stop, beta, alpha (S16, S19)
+//   P4  t = A what                                                  (S18)
+// Once the stop flag is set, every later kernel returns at once.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace rbs {
+
+constexpr int SQ = 4;  // window placements used by the solver kernels
+
+struct Ctx {
+    CSRView A;
+    int64_t n;
+    double *x, *r, *r0, *p, *ph, *s, *q, *qh, *y, *invd;
+    double *rh, *w, *wh, *t, *sh, *z, *zh, *v;
+    const double *b, *x0;
+    SolverState *st;
+    DotScratch *g;
+    double *hist;
+    unsigned *err;
+};
+
+// ---- scalar tails (one thread of the last block) ------------------------------
+
+__device__ __forceinline__ void rec_begin(SolverState *st) {
+    for (int f = 0; f < RBS_HIST_W; f++) st->rec[f] = qnan();
+}
+__device__ __forceinline__ void rec_commit(SolverState *st, double *hist) {
+    const int j = st->iter - 1;
+    if (j >= 0 && j < st->hist_cap)
+        for (int f = 0; f < RBS_HIST_W; f++) hist[(int64_t)j * RBS_HIST_W + f] = st->rec[f];
+}
+__device__ __forceinline__ void stop(SolverState *st, int status) {
+    st->status = status;
+    st->done = 1;
+}
+
+// set-up, classic: rho = <r0,r0>, tau0 = sqrt(rho), tau_max = tol * tau0
+__device__ void tail_cls_setup(SolverState *st, const double *v) {
+    const double rho = v[0];
+    const double tau = __dsqrt_rn(rho);
+    st->rho = rho;
+    st->rho0 = rho;
+    st->tau = tau;
+    st->tau0 = tau;
+    st->tau_max = __dmul_rn(st->tol, tau);
+    st->iter = 0;
+    st->status = RBS_OK;
+    st->done = 0;
+    if (!finite_d(tau)) stop(st, RBS_ENAN);
+    else if (!(tau > st->tau_max) || st->maxit <= 0) st->done = 1;
+}
+
+// S3: alpha = rho / <r0, s>
+__device__ void tail_cls_alpha(SolverState *st, const double *v) {
+    rec_begin(st);
+    const double sigma = v[0];
+    st->rec[0] = sigma;
+    if (sigma == 0.0) { stop(st, RBS_EBREAKDOWN); return; }
+    const double alpha = __ddiv_rn(st->rho, sigma);
+    st->rec[1] = alpha;
+    if (!finite_d(alpha)) { stop(st, RBS_ENAN); return; }
+    st->alpha = alpha;
+}
+
+// S7: omega = <q,y> / <y,y> (0 when y == 0)
+__device__ void tail_cls_omega(SolverState *st, const double *v) {
+    const double gamma = v[0], delta = v[1];
+    const double omega = (delta == 0.0) ? 0.0 : __ddiv_rn(gamma, delta);
+    st->rec[2] = gamma;
+    st->rec[3] = delta;
+    st->rec[4] = omega;
+    st->omega = omega;
+}
+
+// S10, S11 and the while test
+__device__ void tail_cls_beta(SolverState *st, const double *v, double *hist) {
+    const double rho1 = v[0], theta = v[1];
+    const double tau = __dsqrt_rn(theta);
+    st->rec[5] = rho1;
+    st->rec[6] = theta;
+    st->rec[7] = tau;
+    st->iter += 1;
+    st->tau = tau;
+    const double gamma = st->rec[2], delta = st->rec[3], omega = st->omega;
+    if (!finite_d(gamma) || !finite_d(delta) || !finite_d(omega) || !finite_d(rho1) || !finite_d(theta) ||
+        !finite_d(tau)) {
+        rec_commit(st, hist);
+        stop(st, RBS_ENAN);
+        return;
+    }
+    if (!(tau > st->tau_max)) { rec_commit(st, hist); st->done = 1; return; }
+    if (omega == 0.0 || rho1 == 0.0) { rec_commit(st, hist); stop(st, RBS_EBREAKDOWN); return; }
+    const double beta = __dmul_rn(__ddiv_rn(rho1, st->rho), __ddiv_rn(st->alpha, omega));
+    st->rec[8] = beta;
+    rec_commit(st, hist);
+    if (!finite_d(beta)) { stop(st, RBS_ENAN); return; }
+    st->beta = beta;
+    st->rho = rho1;
+    if (st->iter >= st->maxit) st->done = 1;
+}
+
+// set-up, pipelined: rho = <r0,r0>, mu = <r0,w0>, alpha0 = rho / mu
+__device__ void tail_pipe_setup(SolverState *st, const double *v) {
+    const double rho = v[0], mu = v[1];
+    const double tau = __dsqrt_rn(rho);
+    st->rho = rho;
+    st->rho0 = rho;
+    st->mu0 = mu;
+    st->tau = tau;
+    st->tau0 = tau;
+    st->tau_max = __dmul_rn(st->tol, tau);
+    st->alpha0 = qnan();
+    st->beta = 0.0;
+    st->omega = 0.0;
+    st->iter = 0;
+    st->status = RBS_OK;
+    st->done = 0;
+    if (!finite_d(tau) || !finite_d(mu)) { stop(st, RBS_ENAN); return; }
+    if (!(tau > st->tau_max) || st->maxit <= 0) { st->done = 1; return; }
+    if (mu == 0.0) { stop(st, RBS_EBREAKDOWN); return; }
+    const double alpha = __ddiv_rn(rho, mu);
+    st->alpha = alpha;
+    st->alpha0 = alpha;
+    if (!finite_d(alpha)) stop(st, RBS_ENAN);
+}
+
+// S8 + S11: omega = <q,y> / <y,y>
+__device__ void tail_pipe_omega(SolverState *st, const double *v) {
+    rec_begin(st);
+    const double gamma = v[0], delta = v[1];
+    const double omega = (delta == 0.0) ? 0.0 : __ddiv_rn(gamma, delta);
+    st->rec[0] = gamma;
+    st->rec[1] = delta;
+    st->rec[2] = omega;
+    st->omega = omega;
+}
+
+// S16 + S19 and the while test
+__device__ void tail_pipe_beta(SolverState *st, const double *v, double *hist) {
+    const double rho1 = v[0], a = v[1], c = v[2], e = v[3], theta = v[4];
+    const double tau = __dsqrt_rn(theta);
+    st->rec[3] = rho1;
+    st->rec[4] = a;
+    st->rec[5] = c;
+    st->rec[6] = e;
+    st->rec[7] = theta;
+    st->rec[8] = tau;
+    st->iter += 1;
+    st->tau = tau;
+    const double gamma = st->rec[0], delta = st->rec[1], omega = st->omega;
+    if (!finite_d(gamma) || !finite_d(delta) || !finite_d(omega) || !finite_d(rho1) || !finite_d(a) ||
+        !finite_d(c) || !finite_d(e) || !finite_d(theta) || !finite_d(tau)) {
+        rec_commit(st, hist);
+        stop(st, RBS_ENAN);
+        return;
+    }
+    if (!(tau > st->tau_max)) { rec_commit(st, hist); st->done = 1; return; }
+    if (omega == 0.0 || rho1 == 0.0) { rec_commit(st, hist); stop(st, RBS_EBREAKDOWN); return; }
+    const double beta = __dmul_rn(__ddiv_rn(rho1, st->rho), __ddiv_rn(st->alpha, omega));
+    const double bw = __dmul_rn(beta, omega);
+    const double den = fma(-bw, e, fma(beta, c, a));
+    st->rec[9] = beta;
+    st->rec[10] = den;
+    if (den == 0.0) { rec_commit(st, hist); stop(st, RBS_EBREAKDOWN); return; }
+    const double alpha = __ddiv_rn(rho1, den);
+    st->rec[11] = alpha;
+    rec_commit(st, hist);
+    if (!finite_d(beta) || !finite_d(den) || !finite_d(alpha)) { stop(st, RBS_ENAN); return; }
+    st->beta = beta;
+    st->alpha = alpha;
+    st->rho = rho1;
+    if (st->iter >= st->maxit) st->done = 1;
+}
+
+// ---- classic kernels -------------------------------------------------------------
+
+// set-up: r = b - A x0 (or b), x = x0 (or +0), r0 = p = r, phat = r*invd, <r0,r0>
+template <class R>
+__global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
+    R red;
+    red.init();
+    bool bad = false;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        double ri;
+        if (c.x0) {
+            const double ax = spmv_row(c.A, i, c.x0, bad);
+            ri = __dsub_rn(c.b[i], ax);
+            c.x[i] = c.x0[i];
+        } else {
+            ri = c.b[i];
+            c.x[i] = 0.0;
+        }
+        c.r[i] = ri;
+        c.r0[i] = ri;
+        c.p[i] = ri;
+        c.ph[i] = __dmul_rn(ri, c.invd[i]);
+        red.add(0, ri, ri);
+    }
+    if (bad) atomicOr(c.err, 1u);
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_setup(c.st, vals);
+}
+
+// K1: s = A phat, <r0, s>
+template <class R>
+__global__ void __launch_bounds__(256) k_cls_k1(Ctx c) {
+    if (c.st->done) return;
+    R red;
+    red.init();
+    bool bad = false;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        const double si = spmv_row(c.A, i, c.ph, bad);
+        c.s[i] = si;
+        red.add(0, c.r0[i], si);
+    }
+    if (bad) atomicOr(c.err, 1u);
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
+}
+
+// K2: q = fma(-alpha, s, r), qhat = q * invd
+__global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
+    if (c.st->done) return;
+    const double na = -c.st->alpha;
+    for_pairs(c.n, [&](int64_t i, bool pair) {
+        if (pair) {
+            const double2 s = ld2(c.s, i), r = ld2(c.r, i), d = ld2(c.invd, i);
+            double2 q, qh;
+            q.x = fma(na, s.x, r.x);
+            q.y = fma(na, s.y, r.y);
+            qh.x = __dmul_rn(q.x, d.x);
+            qh.y = __dmul_rn(q.y, d.y);
+            st2(c.q, i, q);
+            st2(c.qh, i, qh);
+        } else {
+            const double q = fma(na, c.s[i], c.r[i]);
+            c.q[i] = q;
+            c.qh[i] = __dmul_rn(q, c.invd[i]);
+        }
+    });
+}
+
+// K3: y = A qhat, <q, y>, <y, y>
+template <class R>
+__global__ void __launch_bounds__(256) k_cls_k3(Ctx c) {
+    if (c.st->done) return;
+    R red;
+    red.init();
+    bool bad = false;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        const double yi = spmv_row(c.A, i, c.qh, bad);
+        c.y[i] = yi;
+        red.add(0, c.q[i], yi);
+        red.add(1, yi, yi);
+    }
+    if (bad) atomicOr(c.err, 1u);
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
+}
+
+// K4: x = fma(omega, qhat, fma(alpha, phat, x)), r = fma(-omega, y, q), <r0,r>, <r,r>
+template <class R>
+__global__ void __launch_bounds__(256) k_cls_k4(Ctx c) {
+    if (c.st->done) return;
+    R red;
+    red.init();
+    const double al = c.st->alpha, om = c.st->omega, nom = -om;
+    for_pairs(c.n, [&](int64_t i, bool pair) {
+        if (pair) {
+            const double2 qh = ld2(c.qh, i), ph = ld2(c.ph, i), y = ld2(c.y, i), q = ld2(c.q, i),
+                          r0 = ld2(c.r0, i);
+            double2 x = ld2(c.x, i), r;
+            x.x = fma(om, qh.x, fma(al, ph.x, x.x));
+            x.y = fma(om, qh.y, fma(al, ph.y, x.y));
+            r.x = fma(nom, y.x, q.x);
+            r.y = fma(nom, y.y, q.y);
+            st2(c.x, i, x);
+            st2(c.r, i, r);
+            red.add(0, r0.x, r.x);
+            red.add(0, r0.y, r.y);
+            red.add(1, r.x, r.x);
+            red.add(1, r.y, r.y);
+        } else {
+            c.x[i] = fma(om, c.qh[i], fma(al, c.ph[i], c.x[i]));
+            const double r = fma(nom, c.y[i], c.q[i]);
+            c.r[i] = r;
+            red.add(0, c.r0[i], r);
+            red.add(1, r, r);
+        }
+    });
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_beta(c.st, vals, c.hist);
+}
+
+// K5: p = fma(beta, fma(-omega, s, p), r), phat = p * invd
+__global__ void __launch_bounds__(256) k_cls_k5(Ctx c) {
+    if (c.st->done) return;
+    const double be = c.st->beta, nom = -c.st->omega;
+    for_pairs(c.n, [&](int64_t i, bool pair) {
+        if (pair) {
+            const double2 s = ld2(c.s, i), r = ld2(c.r, i), d = ld2(c.invd, i);
+            double2 p = ld2(c.p, i), ph;
+            p.x = fma(be, fma(nom, s.x, p.x), r.x);
+            p.y = fma(be, fma(nom, s.y, p.y), r.y);
+            ph.x = __dmul_rn(p.x, d.x);
+            ph.y = __dmul_rn(p.y, d.y);
+            st2(c.p, i, p);
+            st2(c.ph, i, ph);
+        } else {
+            const double p = fma(be, fma(nom, c.s[i], c.p[i]), c.r[i]);
+            c.p[i] = p;
+            c.ph[i] = __dmul_rn(p, c.invd[i]);
+        }
+    });
+}
+
+// ---- pipelined kernels -------------------------------------------------------------
+
+// set-up 1: r = b - A x0 (or b), x, r0 = r, rhat = r * invd
+__global__ void __launch_bounds__(256) k_pipe_setup1(Ctx c) {
+    bool bad = false;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        double ri;
+        if (c.x0) {
+            const double ax = spmv_row(c.A, i, c.x0, bad);
+            ri = __dsub_rn(c.b[i], ax);
+            c.x[i] = c.x0[i];
+        } else {
+            ri = c.b[i];
+            c.x[i] = 0.0;
+        }
+        c.r[i] = ri;
+        c.r0[i] = ri;
+        c.rh[i] = __dmul_rn(ri, c.invd[i]);
+    }
+    if (bad) atomicOr(c.err, 1u);
+}
+
+// set-up 2: w = A rhat, what = w * invd, <r0,r>, <r0,w> -> alpha0
+template <class R>
+__global__ void __launch_bounds__(256) k_pipe_setup2(Ctx c) {
+    R red;
+    red.init();
+    bool bad = false;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        const double wi = spmv_row(c.A, i, c.rh, bad);
+        c.w[i] = wi;
+        c.wh[i] = __dmul_rn(wi, c.invd[i]);
+        const double r0 = c.r0[i];
+        red.add(0, r0, c.r[i]);
+        red.add(1, r0, wi);
+    }
+    if (bad) atomicOr(c.err, 1u);
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
+}
+
+// P1: S1-S4 (copies at iteration 0), S5-S7, S9; <q,y>, <y,y> -> omega
+template <class R>
+__global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
+    if (c.st->done) return;
+    R red;
+    red.init();
+    const double al = c.st->alpha, nal = -al, be = c.st->beta, nom = -c.st->omega;
+    const bool first = c.st->iter == 0;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        double ph, s, sh, z;
+        const double rh = c.rh[i], w = c.w[i], wh = c.wh[i], t = c.t[i];
+        if (first) {
+            ph = rh;
+            s = w;
+            sh = wh;
+            z = t;
+        } else {
+            const double ph0 = c.ph[i], s0 = c.s[i], sh0 = c.sh[i], z0 = c.z[i], zh0 = c.zh[i],
+                         v0 = c.v[i];
+            ph = fma(be, fma(nom, sh0, ph0), rh);
+            s = fma(be, fma(nom, z0, s0), w);
+            sh = fma(be, fma(nom, zh0, sh0), wh);
+            z = fma(be, fma(nom, v0, z0), t);
+        }
+        const double q = fma(nal, s, c.r[i]);
+        const double qh = fma(nal, sh, rh);
+        const double y = fma(nal, z, w);
+        c.ph[i] = ph;
+        c.s[i] = s;
+        c.sh[i] = sh;
+        c.z[i] = z;
+        c.q[i] = q;
+        c.qh[i] = qh;
+        c.y[i] = y;
+        c.zh[i] = __dmul_rn(z, c.invd[i]);
+        red.add(0, q, y);
+        red.add(1, y, y);
+    }
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_omega(c.st, vals);
+}
+
+// P3: S12-S15, S17; <r0,r>, <r0,w>, <r0,s>, <r0,z>, <r,r> -> tau, beta, alpha
+template <class R>
+__global__ void __launch_bounds__(256) k_pipe_p3(Ctx c) {
+    if (c.st->done) return;
+    R red;
+    red.init();
+    const double al = c.st->alpha, nal = -al, om = c.st->omega, nom = -om;
+    for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        const double qh = c.qh[i], y = c.y[i], q = c.q[i];
+        c.x[i] = fma(om, qh, fma(al, c.ph[i], c.x[i]));
+        const double r = fma(nom, y, q);
+        const double rh = fma(nom, fma(nal, c.zh[i], c.wh[i]), qh);
+        const double w = fma(nom, fma(nal, c.v[i], c.t[i]), y);
+        c.r[i] = r;
+        c.rh[i] = rh;
+        c.w[i] = w;
+        c.wh[i] = __dmul_rn(w, c.invd[i]);
+        const double r0 = c.r0[i];
+        red.add(0, r0, r);
+        red.add(1, r0, w);
+        red.add(2, r0, c.s[i]);
+        red.add(3, r0, c.z[i]);
+        red.add(4, r, r);
+    }
+    __shared__ double vals[R::K];
+    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_beta(c.st, vals, c.hist);
+}
+
+// ---- launch -----------------------------------------------------------------------
+
+static Ctx make_ctx(const SolverArgs &a) {
+    Ctx c;
+    c.A = CSRView{a.A.n, a.A.nnz, a.A.rowptr, a.A.col, a.A.val};
+    c.n = a.A.n;
+    c.x = a.v.x; c.r = a.v.r; c.r0 = a.v.r0; c.p = a.v.p; c.ph = a.v.ph; c.s = a.v.s;
+    c.q = a.v.q; c.qh = a.v.qh; c.y = a.v.y; c.invd = a.v.invd;
+    c.rh = a.v.rh; c.w = a.v.w; c.wh = a.v.wh; c.t = a.v.t; c.sh = a.v.sh; c.z = a.v.z;
+    c.zh = a.v.zh; c.v = a.v.v;
+    c.b = a.b; c.x0 = a.x0; c.st = a.st; c.g = a.g; c.hist = a.hist; c.err = a.err;
+    return c;
+}
+
+#define TIMED(kind, launch)             \
+    do {                                \
+        if (tm) tm->before(kind);       \
+        launch;                         \
+        if (tm) tm->after(kind);        \
+    } while (0)
+
+template <class R1, class R2, class R5>
+static cudaError_t setup_t(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *tm) {
+    Ctx c = make_ctx(a);
+    if (variant == RBS_CLASSIC) {
+        TIMED(PK_SETUP, (k_cls_setup<R1><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+    } else {
+        TIMED(PK_SETUP, (k_pipe_setup1<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_SETUP, (k_pipe_setup2<R2><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        TIMED(PK_SETUP, (launch_spmv(a.A, a.v.wh, a.v.t, a.st, a.err, a.spmv, s)));
+    }
+    return cudaGetLastError();
+}
+
+template <class R1, class R2, class R5>
+static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *tm) {
+    Ctx c = make_ctx(a);
+    if (variant == RBS_CLASSIC) {
+        TIMED(PK_SPMV_DOT, (k_cls_k1<R1><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        TIMED(PK_VEC, (k_cls_k2<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_SPMV_DOT, (k_cls_k3<R2><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        TIMED(PK_VEC, (k_cls_k4<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_VEC, (k_cls_k5<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+    } else {
+        TIMED(PK_VEC, (k_pipe_p1<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_SPMV, (launch_spmv(a.A, a.v.zh, a.v.v, a.st, a.err, a.spmv, s)));
+        TIMED(PK_VEC, (k_pipe_p3<R5><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_SPMV, (launch_spmv(a.A, a.v.wh, a.v.t, a.st, a.err, a.spmv, s)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t solver_setup(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t) {
+    if (a.dot_mode == RBS_DOT_PLAIN) return setup_t<PlainR<1>, PlainR<2>, PlainR<5>>(a, variant, s, t);
+    return setup_t<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(a, variant, s, t);
+}
+
+cudaError_t solver_iteration(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t) {
+    if (a.dot_mode == RBS_DOT_PLAIN) return iter_t<PlainR<1>, PlainR<2>, PlainR<5>>(a, variant, s, t);
+    return iter_t<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(a, variant, s, t);
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle h, SolverState *st) {
+    const int loops = st->loops + 1;
+    st->loops = loops;
+    cudaGraphSetConditional(h, (!st->done && loops <= st->maxit + 1) ? 1u : 0u);
+}
+
+cudaError_t launch_set_cond(cudaGraphConditionalHandle h, SolverState *st, cudaStream_t s) {
+    k_set_cond<<<1, 1, 0, s>>>(h, st);
+    return cudaGetLastError();
+}
+
+int solver_blocks_per_sm(int variant, int dot_mode, int which) {
+    int nb = 0;
+    cudaError_t e = cudaSuccess;
+    if (dot_mode == RBS_DOT_PLAIN) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, 256, 0);
+    } else if (variant == RBS_PIPELINED) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, 256, 0);
+    } else if (which == 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k3<ExactR<2, SQ>>, 256, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<ExactR<2, SQ>>, 256, 0);
+    }
+    if (e != cudaSuccess || nb < 1) nb = 1;
+    return nb;
+}
+
+}  // namespace rbs

@@ -1,0 +1,78 @@
+// Host-side interface between the C ABI (capi.cu) and the kernel translation
+// units. Plain C++; no kernel code here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rbs.h"
+
+namespace rbs {
+
+struct DotScratch;
+struct SolverState;
+
+struct CSRArgs {
+    int64_t n, nnz;
+    const int64_t *rowptr;
+    const int32_t *col;
+    const double *val;
+};
+
+struct Cfg {
+    int grid = 0;
+    int block = 256;
+};
+
+// ---- standalone kernels (kernels_dot.cu) ----
+cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,
+                         DotScratch *g, double *out, int window, Cfg cfg, cudaStream_t s);
+cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, DotScratch *g,
+                                 int64_t *limbs, int32_t *flags, int window, Cfg cfg, cudaStream_t s);
+cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, cudaStream_t s);
+cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
+                        unsigned *err, Cfg cfg, cudaStream_t s);
+cudaError_t launch_jacobi_invd(const CSRArgs &A, const double *diag, double *invd, unsigned *err,
+                               Cfg cfg, cudaStream_t s);
+cudaError_t launch_jacobi_apply(int64_t n, const double *invd, const double *p, double *phat, Cfg cfg,
+                                cudaStream_t s);
+cudaError_t launch_csr_check(const CSRArgs &A, unsigned *err, Cfg cfg, cudaStream_t s);
+
+// ---- solver kernels (kernels_solver.cu) ----
+struct SolverVecs {
+    double *x, *r, *r0, *p, *ph, *s, *q, *qh, *y, *invd;  // classic (x, r, r0, q, qh, y, invd shared)
+    double *rh, *w, *wh, *t, *sh, *z, *zh, *v;            // pipelined
+};
+
+struct SolverArgs {
+    CSRArgs A;
+    SolverVecs v;
+    const double *b, *x0;
+    SolverState *st;
+    DotScratch *g;
+    double *hist;
+    unsigned *err;
+    int dot_mode;
+    Cfg vec, spmv;
+};
+
+// Kernel kinds for profiling (rbs_prof.kinds).
+enum ProfKind { PK_SPMV_DOT = 0, PK_VEC = 1, PK_SETUP = 2, PK_SPMV = 3 };
+
+struct KernelTimer {
+    virtual void before(int kind) = 0;
+    virtual void after(int kind) = 0;
+    virtual ~KernelTimer() {}
+};
+
+cudaError_t solver_setup(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t);
+cudaError_t solver_iteration(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t);
+
+// Last node of the graph loop body: keeps the WHILE loop going while the stop
+// flag is clear, and at most maxit + 1 bodies in any case.
+cudaError_t launch_set_cond(cudaGraphConditionalHandle h, SolverState *st, cudaStream_t s);
+
+// occupancy-derived persistent grid for the kernels of one kind
+int solver_blocks_per_sm(int variant, int dot_mode, int which);
+
+}  // namespace rbs

@@ -1,0 +1,90 @@
+"""GPU parity of the fma-ordered CSR SpMV (Sec. 4.1, Sec. 3.3) and the Jacobi
+preconditioner (Sec. 4) against the CPU oracle, bit for bit, including empty
+rows, duplicate entries, signed zeros, the full 128^3 Poisson matrix, launch
+shapes, and a bad column index reported as an error (never read)."""
+import numpy as np
+import pytest
+
+from gpu_common import bits, cuda_device, same_array
+from paper_2302_04180_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return cuda_device()
+
+
+@pytest.fixture(scope="module")
+def rbs(dev):
+    import paper_2302_04180_gb300 as m
+    yield m
+    m.rbs_set_param("spmv.block", 0)
+
+
+def _spmv(rbs, dev, A, x):
+    import torch
+    Ad = rbs.to_device(A, dev)
+    return rbs.rbs_spmv_csr(Ad, torch.from_numpy(x).to(dev)).cpu().numpy()
+
+
+@pytest.mark.parametrize("n,mr,empty,dup", [(1, 1, 0.0, 0.0), (7, 3, 0.3, 0.2), (1000, 12, 0.1, 0.3),
+                                            (33333, 40, 0.05, 0.1)])
+def test_random_csr(rbs, dev, orc, n, mr, empty, dup):
+    A = gen.random_csr(n, mr, seed=n, empty_frac=empty, dup_frac=dup)
+    x = gen.random_vector(n, 3) * 10.0 ** gen.random_vector(n, 3, 9, -100, 100)
+    x[::5] = -0.0
+    assert same_array(_spmv(rbs, dev, A, x), orc.spmv(A, x))
+
+
+@pytest.mark.parametrize("make", [lambda: gen.poisson3d(17), lambda: gen.convdiff3d(19, 10.0),
+                                  lambda: gen.convdiff2d(101, 50.0, (0.6, -0.8))])
+def test_stencils(rbs, dev, orc, make):
+    A = make()
+    x = gen.random_vector(A.n, 5)
+    assert same_array(_spmv(rbs, dev, A, x), orc.spmv(A, x))
+    ones = np.ones(A.n)
+    assert same_array(_spmv(rbs, dev, A, ones), orc.spmv(A, ones))
+
+
+def test_poisson_128_full_size(rbs, dev, orc):
+    A = gen.poisson3d(128)
+    assert A.n == 2097152 and A.nnz == 14581760
+    x = gen.random_vector(A.n, 6)
+    ref = orc.spmv(A, x)
+    for block in (0, 64, 256):
+        rbs.rbs_set_param("spmv.block", block)
+        assert same_array(_spmv(rbs, dev, A, x), ref)
+    rbs.rbs_set_param("spmv.block", 0)
+
+
+def test_bad_column_is_reported_not_read(rbs, dev):
+    import torch
+    A = gen.random_csr(100, 5, seed=1)
+    col = A.col.copy()
+    col[len(col) // 2] = 1 << 30
+    bad = gen.CSR(A.n, A.rowptr, col, A.val)
+    Ad = rbs.to_device(bad, dev)
+    rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+    with pytest.raises(rbs.RbsError) as e:
+        rbs.rbs_stream_status()
+    assert e.value.code == rbs.RBS_EINVAL
+    rbs.rbs_stream_status()  # cleared
+
+
+def test_jacobi(rbs, dev, orc):
+    import torch
+    A = gen.convdiff3d(9, 30.0, (0.2, 1.0, -0.4))
+    Ad = rbs.to_device(A, dev)
+    invd = rbs.rbs_jacobi_invd(Ad)
+    ref = orc.jacobi_invd(A)
+    assert (bits(invd.cpu().numpy()) == bits(ref)).all()
+    p = gen.random_vector(A.n, 2)
+    ph = rbs.rbs_jacobi_apply(invd, torch.from_numpy(p).to(dev))
+    assert (bits(ph.cpu().numpy()) == bits(orc.jacobi_apply(ref, p))).all()
+    d = gen.random_vector(A.n, 3, lo=0.5, hi=2.0)
+    assert (bits(rbs.rbs_jacobi_invd(Ad, torch.from_numpy(d).to(dev)).cpu().numpy())
+            == bits(orc.jacobi_invd(A, d))).all()
+    with pytest.raises(rbs.RbsError):
+        rbs.rbs_jacobi_invd(Ad, torch.zeros(A.n, dtype=torch.float64, device=dev))
