@@ -177,9 +177,12 @@ def run_gpu(args):
     x = torch.empty(A.n, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    loop_mode = 1 if args.loop == "host" else 0
+
     def solve(variant=0, dot_mode=0, profile=False, history=False):
         return rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=variant, x_out=x,
-                             dot_mode=dot_mode, profile=profile, history=history)
+                             dot_mode=dot_mode, profile=profile, history=history,
+                             loop_mode=loop_mode)
 
     for _ in range(args.warmup):
         r0 = solve()
@@ -295,12 +298,15 @@ def run_gpu(args):
 def _traffic():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary (None when absent or stale)."""
-    p = os.path.join(ROOT, "profiles", "traffic_spmv_dot_poisson256.json")
+    p = os.path.join(ROOT, "profiles", "spmv_dot_poisson256_traffic.txt")
     try:
-        with open(p) as f:
-            return json.load(f).get("dram_bytes_per_launch")
+        for line in open(p):
+            if line.startswith("dram_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null", "stale") else float(v)
     except Exception:
-        return None
+        pass
+    return None
 
 
 def _kernel_micro(rbs, gen, dev):
@@ -347,6 +353,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--grid", type=int, default=256,
                     help="Poisson grid side (profiling runs on smaller cases; the metric is 256)")
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="solver loop driver for untimed solves (timed solves use the host "
+                         "driver, which records per-kernel CUDA events)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip e2e, comparators and kernel microbenchmarks")
     args = ap.parse_args()

@@ -207,7 +207,8 @@ int rbs_stream_status(void *stream);
 int rbs_release(void);
 /* Launch-shape knobs for tuning and for configuration-independence tests.
  * Names: "exdot.grid", "exdot.block", "exdot.window" (0 = auto),
- * "spmv.block", "vec.grid", "vec.block". Results never depend on them. */
+ * "spmv.block", "spmv.mode" (0 warp-staged rows, 1 one thread per row),
+ * "vec.grid", "vec.block", "solve.check_every". Results never depend on them. */
 int rbs_set_param(const char *name, int64_t value);
 int64_t rbs_get_param(const char *name);
 const char *rbs_last_error(void);

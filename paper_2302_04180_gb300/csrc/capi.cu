@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // ---- knobs -------------------------------------------------------------------------
 std::atomic<int64_t> p_exdot_grid{0}, p_exdot_block{0}, p_exdot_window{0}, p_spmv_block{0},
-    p_vec_grid{0}, p_vec_block{0}, p_check_every{0};
+    p_vec_grid{0}, p_vec_block{0}, p_check_every{0}, p_spmv_mode{0};
 
 std::atomic<int64_t> *param_slot(const char *name) {
     if (!name) return nullptr;
@@ -45,6 +45,7 @@ std::atomic<int64_t> *param_slot(const char *name) {
     if (!strcmp(name, "vec.grid")) return &p_vec_grid;
     if (!strcmp(name, "vec.block")) return &p_vec_block;
     if (!strcmp(name, "solve.check_every")) return &p_check_every;
+    if (!strcmp(name, "spmv.mode")) return &p_spmv_mode;
     return nullptr;
 }
 
@@ -442,6 +443,7 @@ int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream) {
     std::lock_guard<std::mutex> lk(w->mu);
     CSRArgs a{A->n, A->nnz, A->rowptr, A->col, A->val};
     Cfg c = grid_for(w, A->n, block_of(p_spmv_block.load(), 256), 8);
+    c.mode = p_spmv_mode.load() == 1 ? 1 : 0;
     CK(launch_spmv(a, x, y, nullptr, &w->g->err, c, w->stream));
     return RBS_OK;
 }
@@ -554,6 +556,7 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         if (p_vec_grid.load() > 0) a.vec.grid = (int)p_vec_grid.load();
         const int sb = block_of(p_spmv_block.load(), 256);
         a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0));
+        a.spmv.mode = p_spmv_mode.load() == 1 ? 1 : 0;
         // window headroom: at most 2^20 products per thread per launch
         const int64_t minv = (n + ((int64_t)a.vec.block << 20) - 1) / ((int64_t)a.vec.block << 20);
         if (a.vec.grid < minv) a.vec.grid = (int)minv;

@@ -194,6 +194,117 @@ __device__ __forceinline__ void exact_add(Win<Q> &W, uint32_t &flags, unsigned l
     smem_deposit(sacc, u, L, m);
 }
 
+// Two windows per thread: H takes the product if it fits; a product above H
+// re-anchors H at it and the old H becomes the low window L; a product below H
+// goes to L (anchoring or re-anchoring it when it is empty or lies between L and
+// H); only products below both go to shared memory. Wide-exponent sums (the
+// ill-conditioned dots) then rarely touch shared memory.
+template <int Q>
+__device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flags, unsigned long long *sacc,
+                                           double x, double y) {
+    const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+    const uint32_t yh = (uint32_t)__double2hiint(y), yl = (uint32_t)__double2loint(y);
+    const uint32_t ex = (xh >> 20) & 0x7ffu, ey = (yh >> 20) & 0x7ffu;
+    if (ex == 0x7ffu || ey == 0x7ffu) {
+        flags |= special_flags(xh, xl, yh, yl);
+        return;
+    }
+    const uint32_t A1 = (xh & 0xfffffu) | (ex ? 0x100000u : 0u);
+    const uint32_t B1 = (yh & 0xfffffu) | (ey ? 0x100000u : 0u);
+    if ((A1 | xl) == 0u || (B1 | yl) == 0u) return;
+    const int pos = (int)max(ex, 1u) + (int)max(ey, 1u) - 2;
+    const unsigned long long m00 = (unsigned long long)xl * yl;
+    const unsigned long long m01 = (unsigned long long)xl * B1 + (m00 >> 32);
+    const unsigned long long m10 = (unsigned long long)A1 * yl + (uint32_t)m01;
+    const unsigned long long m11 =
+        (unsigned long long)A1 * B1 + (unsigned long long)((uint32_t)(m01 >> 32) + (uint32_t)(m10 >> 32));
+    const uint32_t p0 = (uint32_t)m00, p1 = (uint32_t)m10, p2 = (uint32_t)m11, p3 = (uint32_t)(m11 >> 32);
+    const uint32_t m = (uint32_t)((int32_t)(xh ^ yh) >> 31);
+    const int L = pos >> 5;
+    uint32_t u[5];
+    shift5(p0, p1, p2, p3, (uint32_t)pos & 31u, u);
+    const int q = L - H.a;
+    if ((unsigned)q < (unsigned)Q) {
+        win_place_add<Q>(H, u, q, m);
+        return;
+    }
+    const int back = Q >= 2 ? Q - 2 : 0;
+    if (q >= Q) {
+        if (H.a != WIN_EMPTY) {
+            win_flush<Q>(Lw, sacc);
+            Lw = H;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) H.w[k] = 0u;
+        H.a = L - back < 0 ? 0 : L - back;
+        win_place_add<Q>(H, u, L - H.a, m);
+        return;
+    }
+    const int ql = L - Lw.a;
+    if ((unsigned)ql < (unsigned)Q) {
+        win_place_add<Q>(Lw, u, ql, m);
+        return;
+    }
+    if (ql >= Q) {
+        win_flush<Q>(Lw, sacc);
+        Lw.a = L - back < 0 ? 0 : L - back;
+        win_place_add<Q>(Lw, u, L - Lw.a, m);
+        return;
+    }
+    smem_deposit(sacc, u, L, m);
+}
+
+// Warp-cooperative flush of every lane's window (all 32 lanes call it). The
+// lanes' windows usually sit on the same few limbs, so per-lane atomics would
+// collide 32 ways. Instead each lane stages its 8 carry-save limbs (words 0..6
+// unsigned, word 7 signed) in shared memory, lane j sums the warp's
+// contributions to limb base + j (at most 32 x 2^32 in magnitude), and one
+// conflict-free atomic per limb lands in the block accumulator. Windows spread
+// over more than 32 limbs fall back to per-lane atomics.
+constexpr int MAX_WARPS = 8;         // every kernel here runs blocks of at most 256 threads
+constexpr int WARP_SCRATCH = 3072;   // bytes of shared memory private to each warp
+
+// Each warp's private slice of one shared buffer. Phases of a kernel that
+// stage data per warp (SpMV operands, then the window flush) reuse it; a warp
+// only ever touches its own slice, so no block barrier is needed between them.
+__device__ __forceinline__ unsigned char *warp_scratch() {
+    __shared__ __align__(16) unsigned char buf[MAX_WARPS * WARP_SCRATCH];
+    return buf + (threadIdx.x >> 5) * WARP_SCRATCH;
+}
+
+template <int Q>
+__device__ __forceinline__ void warp_flush(Win<Q> &W, unsigned long long *sacc) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool has = W.a >= 0;
+    const int lo = __reduce_min_sync(FULL, (unsigned)(has ? W.a : 0x7fffffff));
+    const int hi = (int)__reduce_max_sync(FULL, (unsigned)(has ? W.a : 0));
+    if (lo == 0x7fffffff) return;  // no lane holds a window
+    if (hi - lo > 24) {
+        win_flush<Q>(W, sacc);
+        return;
+    }
+    __syncwarp();
+    long long(*st)[8] = reinterpret_cast<long long(*)[8]>(warp_scratch());  // 2 KB
+    int *off = reinterpret_cast<int *>(warp_scratch() + 32 * 8 * 8);          // 128 B
+#pragma unroll
+    for (int k = 0; k < 7; k++) st[lane][k] = has ? (long long)W.w[k] : 0ll;
+    st[lane][7] = has ? (long long)(int32_t)W.w[7] : 0ll;
+    off[lane] = has ? W.a - lo : 0;
+    __syncwarp();
+    long long sum = 0;
+#pragma unroll 8
+    for (int l = 0; l < 32; l++) {
+        const int k = lane - off[l];
+        if (k >= 0 && k < 8) sum += st[l][k];
+    }
+    __syncwarp();
+    if (sum && lo + lane < NL) atomicAdd(&sacc[lo + lane], (unsigned long long)sum);
+#pragma unroll
+    for (int k = 0; k < 8; k++) W.w[k] = 0u;
+    W.a = WIN_EMPTY;
+}
+
 // ---- block- and grid-level reduction ------------------------------------------
 
 // Zero the block accumulators (K of them). All threads call it; ends in a barrier.
@@ -289,7 +400,7 @@ __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)
                                              long long *limbs_out = nullptr, int32_t *flags_out = nullptr) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        win_flush<Q>(win[k], sacc[k]);
+        warp_flush<Q>(win[k], sacc[k]);
         if (flags[k]) atomicOr(&sflags[k], flags[k]);
     }
     __syncthreads();

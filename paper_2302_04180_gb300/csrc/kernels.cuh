@@ -2,6 +2,8 @@
 // fma-ordered row product, pair-wise vector traversal.
 #pragma once
 
+#include <cuda_pipeline.h>
+
 #include "reduce.cuh"
 
 namespace rbs {
@@ -35,8 +37,96 @@ __device__ __forceinline__ double spmv_row(const CSRView &A, int64_t i, const do
     return acc;
 }
 
+// Warp-staged SpMV: each warp takes 32 consecutive rows, copies their
+// contiguous nonzero span (col, val) into shared memory with coalesced
+// asynchronous copies, then every lane runs its own row: it issues the x
+// gathers of up to 8 entries at once and then the fma chain in stored order.
+// The arithmetic is exactly spmv_row's; only the memory schedule differs.
+// Spans longer than SPMV_CAP (or malformed rows) take the per-lane path.
+// fn(row, y_row) runs in the owning lane. Blocks must be SPMV_WARPS warps or fewer.
+constexpr int SPMV_CAP = 256;
+constexpr int SPMV_WARPS = 8;
+
+template <class F>
+__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x, bool &bad,
+                                               F &&fn) {
+    static_assert(SPMV_CAP * (sizeof(int32_t) + sizeof(double)) <= WARP_SCRATCH, "warp scratch");
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int32_t *scol = reinterpret_cast<int32_t *>(warp_scratch());
+    double *sval = reinterpret_cast<double *>(warp_scratch() + SPMV_CAP * sizeof(int32_t));
+    for (int64_t rb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; rb < A.n; rb += nwarps * 32) {
+        const int64_t r = rb + lane;
+        const bool live = r < A.n;
+        long long b = 0, e = 0;
+        if (live) {
+            b = A.rowptr[r];
+            e = A.rowptr[r + 1];
+        }
+        const int last = (int)((A.n - 1 - rb) < 31 ? (A.n - 1 - rb) : 31);
+        const long long B = __shfl_sync(FULL, b, 0);
+        const long long E = __shfl_sync(FULL, e, last);
+        const bool ok = !live || (b >= B && e >= b && e <= E);
+        const long long span = E - B;
+        const bool staged = __all_sync(FULL, ok) && B >= 0 && E <= A.nnz && span >= 0 && span <= SPMV_CAP;
+        double acc = 0.0;
+        if (staged) {
+            for (int t = lane; t < (int)span; t += 32) {
+                __pipeline_memcpy_async(scol + t, A.col + B + t, sizeof(int32_t));
+                __pipeline_memcpy_async(sval + t, A.val + B + t, sizeof(double));
+            }
+            __pipeline_commit();
+            __pipeline_wait_prior(0);
+            __syncwarp();
+            if (live) {
+                const int lo = (int)(b - B), hi = (int)(e - B);
+                for (int k0 = lo; k0 < hi; k0 += 8) {
+                    double xv[8], av[8];
+                    bool use[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        use[j] = false;
+                        xv[j] = 0.0;
+                        av[j] = 0.0;
+                        if (k0 + j < hi) {
+                            const int32_t c = scol[k0 + j];
+                            av[j] = sval[k0 + j];
+                            if ((uint64_t)(int64_t)c < (uint64_t)A.n) {
+                                xv[j] = __ldg(x + c);
+                                use[j] = true;
+                            } else {
+                                bad = true;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 8; j++)
+                        if (use[j]) acc = fma(av[j], xv[j], acc);
+                }
+            }
+            __syncwarp();
+        } else if (live) {
+            acc = spmv_row(A, r, x, bad);
+        }
+        if (live) fn(r, acc);
+    }
+}
+
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// Row traversal of y = A x with epilogue fn(row, y_row): mode 0 warp-staged,
+// mode 1 one thread per row. Same bits either way.
+template <class F>
+__device__ __forceinline__ void spmv_each(const CSRView &A, const double *__restrict__ x, int mode, bool &bad,
+                                          F &&fn) {
+    if (mode == 0) {
+        spmv_warp_rows(A, x, bad, fn);
+    } else {
+        for (int64_t i = gtid(); i < A.n; i += gstride()) fn(i, spmv_row(A, i, x, bad));
+    }
+}
 
 __device__ __forceinline__ double2 ld2(const double *p, int64_t i) {
     return *reinterpret_cast<const double2 *>(p + i);

@@ -16,7 +16,7 @@ struct DotArgs {
 template <int K, int Q, bool EXPORT>
 __global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool aligned, DotScratch *g,
                                               double *out, long long *limbs, int32_t *flags_out) {
-    ExactR<K, Q> red;
+    ExactR2<K, Q> red;
     red.init();
     if (aligned) {
         const int64_t n2 = n >> 1, st = gstride();
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool ali
     }
     __shared__ double vals[K];
     if (EXPORT) {
+        red.flush_low();
         exact_finish<K, Q>(red.win, red.flags, red.sacc, red.sflags, g, vals, true, limbs, flags_out);
     } else {
         if (red.finish(g, vals) && threadIdx.x < K) out[threadIdx.x] = vals[threadIdx.x];
@@ -126,11 +127,11 @@ cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, doubl
 
 // y = A x (Sec. 4.1), one thread per row, rows in a grid-stride loop. With a
 // solver state, the kernel is a no-op once the solver has stopped.
-__global__ void __launch_bounds__(256) k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y,
-                                              const SolverState *st, unsigned *err) {
+__global__ void __launch_bounds__(256, 4) k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y,
+                                              const SolverState *st, unsigned *err, int mode) {
     if (st && st->done) return;
     bool bad = false;
-    for (int64_t i = gtid(); i < A.n; i += gstride()) y[i] = spmv_row(A, i, x, bad);
+    spmv_each(A, x, mode, bad, [&](int64_t i, double v) { y[i] = v; });
     if (bad) atomicOr(err, 1u);
 }
 
@@ -138,7 +139,7 @@ static CSRView view(const CSRArgs &A) { return CSRView{A.n, A.nnz, A.rowptr, A.c
 
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s) {
-    k_spmv<<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err);
+    k_spmv<<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
     return cudaGetLastError();
 }
 

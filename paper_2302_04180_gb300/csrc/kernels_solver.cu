@@ -35,6 +35,7 @@ struct Ctx {
     DotScratch *g;
     double *hist;
     unsigned *err;
+    int spmv_mode;
 };
 
 // ---- scalar tails (one thread of the last block) ------------------------------
@@ -221,16 +222,15 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
 
 // K1: s = A phat, <r0, s>
 template <class R>
-__global__ void __launch_bounds__(256) k_cls_k1(Ctx c) {
+__global__ void __launch_bounds__(256, 4) k_cls_k1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     bool bad = false;
-    for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        const double si = spmv_row(c.A, i, c.ph, bad);
+    spmv_each(c.A, c.ph, c.spmv_mode, bad, [&](int64_t i, double si) {
         c.s[i] = si;
         red.add(0, c.r0[i], si);
-    }
+    });
     if (bad) atomicOr(c.err, 1u);
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
@@ -260,17 +260,16 @@ __global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
 
 // K3: y = A qhat, <q, y>, <y, y>
 template <class R>
-__global__ void __launch_bounds__(256) k_cls_k3(Ctx c) {
+__global__ void __launch_bounds__(256, 4) k_cls_k3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     bool bad = false;
-    for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        const double yi = spmv_row(c.A, i, c.qh, bad);
+    spmv_each(c.A, c.qh, c.spmv_mode, bad, [&](int64_t i, double yi) {
         c.y[i] = yi;
         red.add(0, c.q[i], yi);
         red.add(1, yi, yi);
-    }
+    });
     if (bad) atomicOr(c.err, 1u);
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
@@ -360,14 +359,13 @@ __global__ void __launch_bounds__(256) k_pipe_setup2(Ctx c) {
     R red;
     red.init();
     bool bad = false;
-    for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        const double wi = spmv_row(c.A, i, c.rh, bad);
+    spmv_each(c.A, c.rh, c.spmv_mode, bad, [&](int64_t i, double wi) {
         c.w[i] = wi;
         c.wh[i] = __dmul_rn(wi, c.invd[i]);
         const double r0 = c.r0[i];
         red.add(0, r0, c.r[i]);
         red.add(1, r0, wi);
-    }
+    });
     if (bad) atomicOr(c.err, 1u);
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
@@ -454,6 +452,7 @@ static Ctx make_ctx(const SolverArgs &a) {
     c.rh = a.v.rh; c.w = a.v.w; c.wh = a.v.wh; c.t = a.v.t; c.sh = a.v.sh; c.z = a.v.z;
     c.zh = a.v.zh; c.v = a.v.v;
     c.b = a.b; c.x0 = a.x0; c.st = a.st; c.g = a.g; c.hist = a.hist; c.err = a.err;
+    c.spmv_mode = a.spmv.mode;
     return c;
 }
 

@@ -22,6 +22,7 @@ struct CSRArgs {
 struct Cfg {
     int grid = 0;
     int block = 256;
+    int mode = 0;  // SpMV row schedule: 0 warp-staged, 1 thread per row
 };
 
 // ---- standalone kernels (kernels_dot.cu) ----

@@ -40,6 +40,42 @@ struct ExactR {
     }
 };
 
+// ExactR with a second (low) window per dot: for standalone dots, whose
+// operands may span far more exponents than the solver's vectors.
+template <int K_, int Q>
+struct ExactR2 {
+    static constexpr int K = K_;
+    Win<Q> win[K], low[K];
+    uint32_t flags[K];
+    unsigned long long (*sacc)[NL];
+    uint32_t *sflags;
+
+    __device__ __forceinline__ void init() {
+        __shared__ unsigned long long s_acc[K][NL];
+        __shared__ uint32_t s_flags[K];
+        sacc = s_acc;
+        sflags = s_flags;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            win[k].init();
+            low[k].init();
+            flags[k] = 0u;
+        }
+        sacc_zero<K>(sacc, sflags);
+    }
+    __device__ __forceinline__ void add(int k, double x, double y) {
+        exact_add2<Q>(win[k], low[k], flags[k], sacc[k], x, y);
+    }
+    __device__ __forceinline__ void flush_low() {
+#pragma unroll
+        for (int k = 0; k < K; k++) warp_flush<Q>(low[k], sacc[k]);
+    }
+    __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
+        flush_low();
+        return exact_finish<K, Q>(win, flags, sacc, sflags, g, vals);
+    }
+};
+
 template <int K_>
 struct PlainR {
     static constexpr int K = K_;

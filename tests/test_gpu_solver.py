@@ -21,7 +21,7 @@ def dev():
 def rbs(dev):
     import paper_2302_04180_gb300 as m
     yield m
-    for k in ("vec.grid", "vec.block", "spmv.block", "solve.check_every"):
+    for k in ("vec.grid", "vec.block", "spmv.block", "spmv.mode", "solve.check_every"):
         m.rbs_set_param(k, 0)
 
 
@@ -86,8 +86,9 @@ def test_x0_and_given_diagonal(rbs, dev, orc, variant):
 def test_launch_shape_and_chunk_independence(rbs, dev, orc):
     A = gen.convdiff3d(14, 10.0)
     o = orc.solve(A, orc.spmv(A, np.ones(A.n)), tol=1e-10, maxit=500, variant=0)
-    for vg, vb, sb, ce, lm in ((0, 0, 0, 0, 0), (0, 0, 0, 0, 1), (1, 32, 32, 1, 1), (7, 128, 64, 3, 0),
-                               (500, 256, 256, 50, 1), (152, 64, 128, 0, 0)):
+    for vg, vb, sb, ce, lm, sm in ((0, 0, 0, 0, 0, 0), (0, 0, 0, 0, 1, 1), (1, 32, 32, 1, 1, 0),
+                                   (7, 128, 64, 3, 0, 1), (500, 256, 256, 50, 1, 0), (152, 64, 128, 0, 0, 1)):
+        rbs.rbs_set_param("spmv.mode", sm)
         rbs.rbs_set_param("vec.grid", vg)
         rbs.rbs_set_param("vec.block", vb)
         rbs.rbs_set_param("spmv.block", sb)
@@ -96,7 +97,7 @@ def test_launch_shape_and_chunk_independence(rbs, dev, orc):
             ov = o if variant == 0 else orc.solve(A, orc.spmv(A, np.ones(A.n)), tol=1e-10, maxit=500,
                                                   variant=1)
             _assert_same_run(g, ov)
-    for k in ("vec.grid", "vec.block", "spmv.block"):
+    for k in ("vec.grid", "vec.block", "spmv.block", "spmv.mode"):
         rbs.rbs_set_param(k, 0)
 
 

@@ -21,6 +21,7 @@ def rbs(dev):
     import paper_2302_04180_gb300 as m
     yield m
     m.rbs_set_param("spmv.block", 0)
+    m.rbs_set_param("spmv.mode", 0)
 
 
 def _spmv(rbs, dev, A, x):
@@ -35,7 +36,11 @@ def test_random_csr(rbs, dev, orc, n, mr, empty, dup):
     A = gen.random_csr(n, mr, seed=n, empty_frac=empty, dup_frac=dup)
     x = gen.random_vector(n, 3) * 10.0 ** gen.random_vector(n, 3, 9, -100, 100)
     x[::5] = -0.0
-    assert same_array(_spmv(rbs, dev, A, x), orc.spmv(A, x))
+    ref = orc.spmv(A, x)
+    for mode in (0, 1):  # long spans (mr=40) also exercise the staged path's fallback
+        rbs.rbs_set_param("spmv.mode", mode)
+        assert same_array(_spmv(rbs, dev, A, x), ref), mode
+    rbs.rbs_set_param("spmv.mode", 0)
 
 
 @pytest.mark.parametrize("make", [lambda: gen.poisson3d(17), lambda: gen.convdiff3d(19, 10.0),
@@ -53,10 +58,13 @@ def test_poisson_128_full_size(rbs, dev, orc):
     assert A.n == 2097152 and A.nnz == 14581760
     x = gen.random_vector(A.n, 6)
     ref = orc.spmv(A, x)
-    for block in (0, 64, 256):
-        rbs.rbs_set_param("spmv.block", block)
-        assert same_array(_spmv(rbs, dev, A, x), ref)
+    for mode in (0, 1):
+        rbs.rbs_set_param("spmv.mode", mode)
+        for block in (0, 64, 256):
+            rbs.rbs_set_param("spmv.block", block)
+            assert same_array(_spmv(rbs, dev, A, x), ref), (mode, block)
     rbs.rbs_set_param("spmv.block", 0)
+    rbs.rbs_set_param("spmv.mode", 0)
 
 
 def test_bad_column_is_reported_not_read(rbs, dev):
