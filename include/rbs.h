@@ -99,6 +99,23 @@ int rbs_exdot_partial(const double *x, const double *y, int64_t n, int64_t *limb
 /* out = RN(value of the limb array) (host or device out; device limbs). */
 int rbs_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, void *stream);
 
+/* Allocation-free variant of rbs_exdot_multi (the paper has no counterpart; it
+ * is a deployment aid). For callers that cannot allocate when they call: code
+ * running while a CUDA graph is captured, latency-critical loops that cannot
+ * take an allocation's implicit synchronisation, applications whose own pool
+ * owns the device memory. Same results, bit for bit, as rbs_exdot_multi.
+ * Its scratch is one 8 KiB file-scope device array inside the library, held
+ * by every GPU that loads the library until the process exits; it holds at most
+ * RBS_NOALLOC_MAX_DOTS accumulators, and larger k returns RBS_EINVAL. xs, ys
+ * (host arrays of device pointers), out (k binary64): device memory only.
+ * The first call on a device sets up that device (finds the array's device
+ * address and clears it, synchronously): make it before any stream capture.
+ * Every call clears the array on `stream` before use. All calls on a device
+ * share the array, so calls that overlap on the GPU race; order them. */
+#define RBS_NOALLOC_MAX_DOTS 6
+int rbs_exdot_noalloc(int k, const double *const *xs, const double *const *ys, int64_t n,
+                      double *out, void *stream);
+
 /* ---- fma-ordered SpMV (Sec. 4.1 "Sparse matrix-vector product"; Sec. 3.3) ----
  * y[i] = fma(val[last], x[col[last]], ... fma(val[first], x[col[first]], +0.0))
  * over row i in stored order, every step rounded to nearest even; an empty row

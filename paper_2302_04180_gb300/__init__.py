@@ -27,12 +27,13 @@ RBS_CLASSIC, RBS_PIPELINED = 0, 1
 RBS_DOT_EXACT, RBS_DOT_PLAIN = 0, 1
 RBS_LOOP_GRAPH, RBS_LOOP_HOST = 0, 1
 RBS_LIMBS = 136
+RBS_NOALLOC_MAX_DOTS = 6
 RBS_HIST_W = 12
 RBS_PROF_KINDS = 8
 PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv")
 
 # every symbol include/rbs.h declares
-EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_partial", "rbs_round_limbs",
+EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
            "rbs_spmv_csr", "rbs_jacobi_invd", "rbs_jacobi_apply", "rbs_solve",
            "rbs_solve_ex", "rbs_stream_status", "rbs_release", "rbs_set_param",
            "rbs_get_param", "rbs_last_error", "rbs_version")
@@ -88,6 +89,7 @@ def load(path: str | None = None):
         sig = {
             "rbs_exdot": [vp, vp, i64, vp, vp],
             "rbs_exdot_multi": [C.c_int, vp, vp, i64, vp, vp],
+            "rbs_exdot_noalloc": [C.c_int, vp, vp, i64, vp, vp],
             "rbs_exdot_partial": [vp, vp, i64, vp, vp, vp],
             "rbs_round_limbs": [vp, vp, vp, vp],
             "rbs_spmv_csr": [C.POINTER(_Csr), vp, vp, vp],
@@ -213,6 +215,17 @@ def rbs_exdot_multi(xs, ys, out=None, stream=None):
         import torch
         out = torch.empty(k, dtype=torch.float64, device=xs[0].device)
     _check(load().rbs_exdot_multi(k, xa, ya, n, _ptr(out), _stream(stream, xs[0], out)))
+    return out
+
+
+def rbs_exdot_noalloc(xs, ys, out, stream=None):
+    """Allocation-free k exact dots: `out` (k float64) and all operands must be
+    device tensors; nothing is allocated on any path of this call."""
+    k = len(xs)
+    xa = (C.c_void_p * k)(*[_ptr(t) for t in xs])
+    ya = (C.c_void_p * k)(*[_ptr(t) for t in ys])
+    _check(load().rbs_exdot_noalloc(k, xa, ya, int(xs[0].shape[0]), _ptr(out),
+                                    _stream(stream, xs[0], out)))
     return out
 
 

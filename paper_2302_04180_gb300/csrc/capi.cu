@@ -294,6 +294,9 @@ int graph_loop(Workspace *w, const SolverArgs &a, int variant) {
 }
 
 }  // namespace
+
+int set_error(int code, const char *msg) { return fail(code, msg); }
+
 }  // namespace rbs
 
 using namespace rbs;

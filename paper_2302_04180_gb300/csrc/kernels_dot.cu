@@ -1,5 +1,7 @@
 // Standalone kernels: exact dot (single and multi-output), long-accumulator
 // export and rounding, fma-ordered SpMV, Jacobi, CSR validation.
+#include <mutex>
+
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -212,3 +214,107 @@ cudaError_t launch_csr_check(const CSRArgs &A, unsigned *err, Cfg cfg, cudaStrea
 }
 
 }  // namespace rbs
+
+// ---- allocation-free exact dot ---------------------------------------------------
+//
+// rbs_exdot_noalloc runs the same exact-dot kernel as rbs_exdot_multi, but keeps
+// its only scratch -- the cross-block long accumulators, flags and ticket --
+// in the file-scope device array below instead of the per-stream workspace, so
+// it never allocates device or pinned host memory. It serves callers that
+// cannot allocate at the point of the call: code running while a CUDA graph is
+// being captured (a cudaMalloc is not a capturable step), latency-critical
+// loops that cannot afford the implicit device synchronisation of an
+// allocation, and applications whose own memory pool owns the device memory.
+//
+// The array is 8 KiB and holds at most RBS_NOALLOC_MAX_DOTS accumulators.
+// Every GPU that loads this library keeps the array until the process exits.
+// All calls on a device share it, so calls that overlap on the GPU (for
+// example on two streams at once) race and must be ordered by the caller.
+namespace rbs {
+namespace {
+
+constexpr size_t NOALLOC_BYTES = 8192;
+static_assert(sizeof(DotScratch) <= NOALLOC_BYTES, "scratch array too small");
+static_assert(RBS_NOALLOC_MAX_DOTS == KMAX, "accumulator count");
+
+static __device__ __align__(256) unsigned char noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex noalloc_mu;
+void *noalloc_ptr[NOALLOC_MAX_DEVICES];
+int noalloc_sms[NOALLOC_MAX_DEVICES];
+
+// Set-up, once per device, with that device current: the array's device
+// address (in host code its name is only a host-side stand-in), a one-time
+// clear, and the SM count for the launch shape.
+int noalloc_setup(int dev, void **ptr, int *sms) {
+    std::lock_guard<std::mutex> lk(noalloc_mu);
+    if (!noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, noalloc_scratch);
+        if (e != cudaSuccess) return set_error(RBS_ECUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return set_error(RBS_ECUDA, "cudaDeviceGetAttribute failed");
+        e = cudaMemset(p, 0, NOALLOC_BYTES);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return set_error(RBS_ECUDA, "clearing the no-alloc scratch failed");
+        noalloc_sms[dev] = n;
+        noalloc_ptr[dev] = p;
+    }
+    *ptr = noalloc_ptr[dev];
+    *sms = noalloc_sms[dev];
+    return RBS_OK;
+}
+
+bool device_resident(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace rbs
+
+extern "C" int rbs_exdot_noalloc(int k, const double *const *xs, const double *const *ys, int64_t n,
+                                 double *out, void *stream) {
+    using namespace rbs;
+    if (k < 1 || k > RBS_NOALLOC_MAX_DOTS)
+        return set_error(RBS_EINVAL, "rbs_exdot_noalloc: k must be 1..RBS_NOALLOC_MAX_DOTS (6), the "
+                                     "accumulators its fixed scratch array holds");
+    if (n < 0 || !xs || !ys || !out) return set_error(RBS_EINVAL, "rbs_exdot_noalloc: bad argument");
+    if (!device_resident(out)) return set_error(RBS_EINVAL, "rbs_exdot_noalloc: out must be device memory");
+    for (int j = 0; j < k; j++)
+        if (n > 0 && (!xs[j] || !ys[j] || !device_resident(xs[j]) || !device_resident(ys[j])))
+            return set_error(RBS_EINVAL, "rbs_exdot_noalloc: operands must be device memory");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return set_error(RBS_ECUDA, "rbs_exdot_noalloc: no usable current device");
+    void *p = nullptr;
+    int sms = 0;
+    int rc = noalloc_setup(dev, &p, &sms);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the shared array keeps the last call's contents: clear it first
+    if (cudaMemsetAsync(p, 0, sizeof(DotScratch), s) != cudaSuccess)
+        return set_error(RBS_ECUDA, "rbs_exdot_noalloc: cudaMemsetAsync failed");
+    if (n == 0) {
+        if (cudaMemsetAsync(out, 0, k * sizeof(double), s) != cudaSuccess)
+            return set_error(RBS_ECUDA, "rbs_exdot_noalloc: cudaMemsetAsync failed");
+        return RBS_OK;
+    }
+    Cfg c;
+    c.block = 256;
+    int64_t g = (n + 2LL * c.block - 1) / (2LL * c.block);
+    const int64_t cap = (int64_t)sms * 4;
+    g = g < 1 ? 1 : (g < cap ? g : cap);
+    const int64_t minimum = (n + ((int64_t)c.block << 20) - 1) / ((int64_t)c.block << 20);
+    if (g < minimum) g = minimum;
+    c.grid = (int)(g > 0x7fffffff ? 0x7fffffff : g);
+    cudaError_t e = exdot_q<4>(k, xs, ys, n, reinterpret_cast<DotScratch *>(p), out, c, s);
+    if (e != cudaSuccess) return set_error(RBS_ECUDA, "rbs_exdot_noalloc: kernel launch failed");
+    return RBS_OK;
+}

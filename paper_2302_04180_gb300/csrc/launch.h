@@ -25,6 +25,9 @@ struct Cfg {
     int mode = 0;  // SpMV row schedule: 0 warp-staged, 1 thread per row
 };
 
+// Set the calling thread's rbs_last_error() message and return `code`.
+int set_error(int code, const char *msg);
+
 // ---- standalone kernels (kernels_dot.cu) ----
 cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,
                          DotScratch *g, double *out, int window, Cfg cfg, cudaStream_t s);
