@@ -262,7 +262,7 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
 // conflict-free atomic per limb lands in the block accumulator. Windows spread
 // over more than 32 limbs fall back to per-lane atomics.
 constexpr int MAX_WARPS = 8;         // every kernel here runs blocks of at most 256 threads
-constexpr int WARP_SCRATCH = 3072;   // bytes of shared memory private to each warp
+constexpr int WARP_SCRATCH = 6144;   // bytes of shared memory private to each warp
 
 // Each warp's private slice of one shared buffer. Phases of a kernel that
 // stage data per warp (SpMV operands, then the window flush) reuse it; a warp

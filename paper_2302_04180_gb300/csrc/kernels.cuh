@@ -37,50 +37,91 @@ __device__ __forceinline__ double spmv_row(const CSRView &A, int64_t i, const do
     return acc;
 }
 
-// Warp-staged SpMV: each warp takes 32 consecutive rows, copies their
-// contiguous nonzero span (col, val) into shared memory with coalesced
-// asynchronous copies, then every lane runs its own row: it issues the x
-// gathers of up to 8 entries at once and then the fma chain in stored order.
-// The arithmetic is exactly spmv_row's; only the memory schedule differs.
-// Spans longer than SPMV_CAP (or malformed rows) take the per-lane path.
-// fn(row, y_row) runs in the owning lane. Blocks must be SPMV_WARPS warps or fewer.
+// Warp-staged SpMV: each warp walks chunks of 32 consecutive rows. A chunk's
+// contiguous nonzero span (col, val) is copied into the warp's shared memory
+// with coalesced asynchronous copies, then every lane runs its own row: it
+// issues the x gathers of up to 8 entries at once, then the fma chain in stored
+// order. The walk is software-pipelined three chunks deep: the row pointers of
+// chunk c+2 are loading and the operands of chunk c+1 are copying (second
+// buffer) while chunk c computes. The arithmetic is exactly spmv_row's; only
+// the memory schedule differs. Spans longer than SPMV_CAP (or malformed row
+// pointers) take the per-lane path. fn(row, y_row) runs in the owning lane.
+// All 32 lanes of every warp must enter; blocks have at most MAX_WARPS warps.
 constexpr int SPMV_CAP = 256;
-constexpr int SPMV_WARPS = 8;
+constexpr int SPMV_BUF = SPMV_CAP * (sizeof(int32_t) + sizeof(double));  // 3 KB per buffer
 
-template <class F>
-__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x, bool &bad,
-                                               F &&fn) {
-    static_assert(SPMV_CAP * (sizeof(int32_t) + sizeof(double)) <= WARP_SCRATCH, "warp scratch");
+struct SpmvChunk {
+    long long B;  // first nonzero of the chunk
+    int span;     // nonzeros in the chunk
+    bool staged;  // operands are in shared memory
+};
+
+// Prepare chunk rb (row pointers b, e of this lane's row already loaded):
+// decide whether it can be staged and issue its copies into buffer `buf`.
+// Always commits one copy group, so group counting stays uniform.
+__device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t rb, long long b, long long e,
+                                                  unsigned char *buf) {
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int32_t *scol = reinterpret_cast<int32_t *>(warp_scratch());
-    double *sval = reinterpret_cast<double *>(warp_scratch() + SPMV_CAP * sizeof(int32_t));
-    for (int64_t rb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; rb < A.n; rb += nwarps * 32) {
-        const int64_t r = rb + lane;
-        const bool live = r < A.n;
-        long long b = 0, e = 0;
-        if (live) {
-            b = A.rowptr[r];
-            e = A.rowptr[r + 1];
-        }
+    const int lane = threadIdx.x & 31;
+    SpmvChunk c{0, 0, false};
+    if (rb < A.n) {
+        const bool live = rb + lane < A.n;
         const int last = (int)((A.n - 1 - rb) < 31 ? (A.n - 1 - rb) : 31);
         const long long B = __shfl_sync(FULL, b, 0);
         const long long E = __shfl_sync(FULL, e, last);
         const bool ok = !live || (b >= B && e >= b && e <= E);
         const long long span = E - B;
-        const bool staged = __all_sync(FULL, ok) && B >= 0 && E <= A.nnz && span >= 0 && span <= SPMV_CAP;
-        double acc = 0.0;
-        if (staged) {
-            for (int t = lane; t < (int)span; t += 32) {
+        c.B = B;
+        c.span = (int)(span > 0 && span <= SPMV_CAP ? span : 0);
+        c.staged = __all_sync(FULL, ok) && B >= 0 && E <= A.nnz && span >= 0 && span <= SPMV_CAP;
+        if (c.staged) {
+            int32_t *scol = reinterpret_cast<int32_t *>(buf);
+            double *sval = reinterpret_cast<double *>(buf + SPMV_CAP * sizeof(int32_t));
+            for (int t = lane; t < c.span; t += 32) {
                 __pipeline_memcpy_async(scol + t, A.col + B + t, sizeof(int32_t));
                 __pipeline_memcpy_async(sval + t, A.val + B + t, sizeof(double));
             }
-            __pipeline_commit();
-            __pipeline_wait_prior(0);
-            __syncwarp();
-            if (live) {
-                const int lo = (int)(b - B), hi = (int)(e - B);
+        }
+    }
+    __pipeline_commit();
+    return c;
+}
+
+template <class F>
+__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x, bool &bad,
+                                               F &&fn) {
+    static_assert(2 * SPMV_BUF <= WARP_SCRATCH, "warp scratch");
+    const int lane = threadIdx.x & 31;
+    const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5) * 32;
+    int64_t rb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    unsigned char *bufs = warp_scratch();
+    auto rowptrs = [&](int64_t r0, long long &b, long long &e) {
+        const int64_t r = r0 + lane;
+        b = 0;
+        e = 0;
+        if (r0 < A.n && r < A.n) {
+            b = A.rowptr[r];
+            e = A.rowptr[r + 1];
+        }
+    };
+    long long b0, e0, b1, e1, b2, e2;
+    rowptrs(rb, b0, e0);
+    SpmvChunk c0 = spmv_prepare(A, rb, b0, e0, bufs);
+    rowptrs(rb + step, b1, e1);
+    int cur = 0;
+    for (; rb < A.n; rb += step) {
+        const SpmvChunk c1 = spmv_prepare(A, rb + step, b1, e1, bufs + (cur ^ 1) * SPMV_BUF);
+        rowptrs(rb + 2 * step, b2, e2);
+        __pipeline_wait_prior(1);  // chunk rb's copies have landed
+        __syncwarp();
+        const int64_t r = rb + lane;
+        if (r < A.n) {
+            double acc = 0.0;
+            if (c0.staged) {
+                const int32_t *scol = reinterpret_cast<const int32_t *>(bufs + cur * SPMV_BUF);
+                const double *sval =
+                    reinterpret_cast<const double *>(bufs + cur * SPMV_BUF + SPMV_CAP * sizeof(int32_t));
+                const int lo = (int)(b0 - c0.B), hi = (int)(e0 - c0.B);
                 for (int k0 = lo; k0 < hi; k0 += 8) {
                     double xv[8], av[8];
                     bool use[8];
@@ -90,10 +131,10 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
                         xv[j] = 0.0;
                         av[j] = 0.0;
                         if (k0 + j < hi) {
-                            const int32_t c = scol[k0 + j];
+                            const int32_t cidx = scol[k0 + j];
                             av[j] = sval[k0 + j];
-                            if ((uint64_t)(int64_t)c < (uint64_t)A.n) {
-                                xv[j] = __ldg(x + c);
+                            if ((uint64_t)(int64_t)cidx < (uint64_t)A.n) {
+                                xv[j] = __ldg(x + cidx);
                                 use[j] = true;
                             } else {
                                 bad = true;
@@ -104,13 +145,21 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
                     for (int j = 0; j < 8; j++)
                         if (use[j]) acc = fma(av[j], xv[j], acc);
                 }
+            } else {
+                acc = spmv_row(A, r, x, bad);
             }
-            __syncwarp();
-        } else if (live) {
-            acc = spmv_row(A, r, x, bad);
+            fn(r, acc);
         }
-        if (live) fn(r, acc);
+        __syncwarp();  // buffer `cur` is refilled two chunks later
+        c0 = c1;
+        b0 = b1;
+        e0 = e1;
+        b1 = b2;
+        e1 = e2;
+        cur ^= 1;
     }
+    __pipeline_wait_prior(0);
+    __syncwarp();
 }
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
 
 // K1: s = A phat, <r0, s>
 template <class R>
-__global__ void __launch_bounds__(256, 4) k_cls_k1(Ctx c) {
+__global__ void __launch_bounds__(256, 3) k_cls_k1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
 
 // K3: y = A qhat, <q, y>, <y, y>
 template <class R>
-__global__ void __launch_bounds__(256, 4) k_cls_k3(Ctx c) {
+__global__ void __launch_bounds__(256, 3) k_cls_k3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
