@@ -225,7 +225,9 @@ int rbs_release(void);
 /* Launch-shape knobs for tuning and for configuration-independence tests.
  * Names: "exdot.grid", "exdot.block", "exdot.window" (0 = auto),
  * "spmv.block", "spmv.mode" (0 warp-staged rows, 1 one thread per row),
- * "vec.grid", "vec.block", "solve.check_every". Results never depend on them. */
+ * "vec.grid", "vec.block", "solve.check_every", "smem.carveout" (percent of
+ * L1/shared storage for the staging kernels; default 75, -1 = driver default).
+ * Results never depend on them. */
 int rbs_set_param(const char *name, int64_t value);
 int64_t rbs_get_param(const char *name);
 const char *rbs_last_error(void);

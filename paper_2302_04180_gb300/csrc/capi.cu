@@ -34,7 +34,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // ---- knobs -------------------------------------------------------------------------
 std::atomic<int64_t> p_exdot_grid{0}, p_exdot_block{0}, p_exdot_window{0}, p_spmv_block{0},
-    p_vec_grid{0}, p_vec_block{0}, p_check_every{0}, p_spmv_mode{0};
+    p_vec_grid{0}, p_vec_block{0}, p_check_every{0}, p_spmv_mode{0}, p_carveout{75};
 
 std::atomic<int64_t> *param_slot(const char *name) {
     if (!name) return nullptr;
@@ -46,6 +46,7 @@ std::atomic<int64_t> *param_slot(const char *name) {
     if (!strcmp(name, "vec.block")) return &p_vec_block;
     if (!strcmp(name, "solve.check_every")) return &p_check_every;
     if (!strcmp(name, "spmv.mode")) return &p_spmv_mode;
+    if (!strcmp(name, "smem.carveout")) return &p_carveout;
     return nullptr;
 }
 
@@ -210,6 +211,15 @@ Cfg exdot_cfg(Workspace *w, int64_t n) {
     if (g > 0x7fffffff) g = 0x7fffffff;
     c.grid = (int)g;
     return c;
+}
+
+// Shared-memory carveout of the staging kernels. Measured on GB300 (Poisson
+// 256^3): 60-75 % of the unified L1/shared storage is best -- enough shared
+// memory for three 256-thread blocks per SM while L1 keeps the SpMV's x
+// gathers; the maximum split costs 25 %, a small one halves throughput.
+int carveout_param() {
+    const int64_t c = p_carveout.load();
+    return (c >= 0 && c <= 100) ? (int)c : -1;
 }
 
 int window_param() {
@@ -447,6 +457,7 @@ int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream) {
     CSRArgs a{A->n, A->nnz, A->rowptr, A->col, A->val};
     Cfg c = grid_for(w, A->n, block_of(p_spmv_block.load(), 256), 8);
     c.mode = p_spmv_mode.load() == 1 ? 1 : 0;
+    c.carveout = carveout_param();
     CK(launch_spmv(a, x, y, nullptr, &w->g->err, c, w->stream));
     return RBS_OK;
 }
@@ -560,6 +571,8 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         const int sb = block_of(p_spmv_block.load(), 256);
         a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0));
         a.spmv.mode = p_spmv_mode.load() == 1 ? 1 : 0;
+        a.carveout = carveout_param();
+        a.spmv.carveout = a.carveout;
         // window headroom: at most 2^20 products per thread per launch
         const int64_t minv = (n + ((int64_t)a.vec.block << 20) - 1) / ((int64_t)a.vec.block << 20);
         if (a.vec.grid < minv) a.vec.grid = (int)minv;

@@ -49,9 +49,8 @@ struct Win {
     }
 };
 
-// w += (v ^ m) + (m & 1) over 8 words: adds v, or subtracts it when m = ~0.
-__device__ __forceinline__ void add8_signed(uint32_t (&w)[8], const uint32_t (&v)[8], uint32_t m) {
-    uint32_t c = m & 1u;
+// w += v + c over 8 words with carry (c in {0, 1}).
+__device__ __forceinline__ void add8_carry(uint32_t (&w)[8], const uint32_t (&v)[8], uint32_t c) {
     asm("{\n\t.reg .u32 t;\n\t"
         "add.cc.u32 t, %8, 0xffffffff;\n\t"
         "addc.cc.u32 %0, %0, %9;\n\t"
@@ -64,8 +63,8 @@ __device__ __forceinline__ void add8_signed(uint32_t (&w)[8], const uint32_t (&v
         "addc.u32 %7, %7, %16;\n\t}"
         : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]), "+r"(w[6]),
           "+r"(w[7])
-        : "r"(c), "r"(v[0] ^ m), "r"(v[1] ^ m), "r"(v[2] ^ m), "r"(v[3] ^ m), "r"(v[4] ^ m),
-          "r"(v[5] ^ m), "r"(v[6] ^ m), "r"(v[7] ^ m));
+        : "r"(c), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+          "r"(v[7]));
 }
 
 // The 106-bit product p (4 words) shifted left by r in [0, 31]: 5 words.
@@ -78,38 +77,46 @@ __device__ __forceinline__ void shift5(uint32_t p0, uint32_t p1, uint32_t p2, ui
     u[4] = __funnelshift_l(p3, 0u, r);
 }
 
-template <int Q>
+// Place the 5-word shifted product at word offset q (log-shifter of word
+// selects) and add it, negated when m = ~0: the placed 8-word value is
+// complemented word by word (the product's words are XORed with m before
+// placement and every fill word is m) and 1 is carried in, which is its
+// two's complement negation.
+template <int Q, bool SIGNED>
 __device__ __forceinline__ void win_place_add(Win<Q> &W, const uint32_t (&u)[5], int q, uint32_t m) {
-    uint32_t v[8];
+    uint32_t x[5], v[8];
+#pragma unroll
+    for (int k = 0; k < 5; k++) x[k] = SIGNED ? (u[k] ^ m) : u[k];
+    const uint32_t f = SIGNED ? m : 0u;
     if (Q == 1) {
-        v[0] = u[0]; v[1] = u[1]; v[2] = u[2]; v[3] = u[3]; v[4] = u[4];
-        v[5] = 0u; v[6] = 0u; v[7] = 0u;
+        v[0] = x[0]; v[1] = x[1]; v[2] = x[2]; v[3] = x[3]; v[4] = x[4];
+        v[5] = f; v[6] = f; v[7] = f;
     } else {
         const bool b1 = (q & 1) != 0;
         uint32_t t[6];
-        t[0] = b1 ? 0u : u[0];
-        t[1] = b1 ? u[0] : u[1];
-        t[2] = b1 ? u[1] : u[2];
-        t[3] = b1 ? u[2] : u[3];
-        t[4] = b1 ? u[3] : u[4];
-        t[5] = b1 ? u[4] : 0u;
+        t[0] = b1 ? f : x[0];
+        t[1] = b1 ? x[0] : x[1];
+        t[2] = b1 ? x[1] : x[2];
+        t[3] = b1 ? x[2] : x[3];
+        t[4] = b1 ? x[3] : x[4];
+        t[5] = b1 ? x[4] : f;
         if (Q == 2) {
 #pragma unroll
             for (int k = 0; k < 6; k++) v[k] = t[k];
-            v[6] = 0u; v[7] = 0u;
+            v[6] = f; v[7] = f;
         } else {
             const bool b2 = (q & 2) != 0;
-            v[0] = b2 ? 0u : t[0];
-            v[1] = b2 ? 0u : t[1];
+            v[0] = b2 ? f : t[0];
+            v[1] = b2 ? f : t[1];
             v[2] = b2 ? t[0] : t[2];
             v[3] = b2 ? t[1] : t[3];
             v[4] = b2 ? t[2] : t[4];
             v[5] = b2 ? t[3] : t[5];
-            v[6] = b2 ? t[4] : 0u;
-            v[7] = b2 ? t[5] : 0u;
+            v[6] = b2 ? t[4] : f;
+            v[7] = b2 ? t[5] : f;
         }
     }
-    add8_signed(W.w, v, m);
+    add8_carry(W.w, v, SIGNED ? (m & 1u) : 0u);
 }
 
 // Add the window into the block accumulator as carry-save limbs: words 0..6
@@ -150,19 +157,21 @@ static __device__ __noinline__ uint32_t special_flags(uint32_t xh, uint32_t xl, 
     return ((xh ^ yh) & 0x80000000u) ? F_NINF : F_PINF;
 }
 
-// Exact accumulation of x*y into window W / block accumulator sacc.
-template <int Q>
+// Exact accumulation of x*y into window W / block accumulator sacc. With
+// SQUARE the product is x*x: it cannot be negative, so no sign handling.
+template <int Q, bool SQUARE = false>
 __device__ __forceinline__ void exact_add(Win<Q> &W, uint32_t &flags, unsigned long long *sacc, double x,
                                           double y) {
     const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
-    const uint32_t yh = (uint32_t)__double2hiint(y), yl = (uint32_t)__double2loint(y);
-    const uint32_t ex = (xh >> 20) & 0x7ffu, ey = (yh >> 20) & 0x7ffu;
+    const uint32_t yh = SQUARE ? xh : (uint32_t)__double2hiint(y);
+    const uint32_t yl = SQUARE ? xl : (uint32_t)__double2loint(y);
+    const uint32_t ex = (xh >> 20) & 0x7ffu, ey = SQUARE ? ex : (yh >> 20) & 0x7ffu;
     if (ex == 0x7ffu || ey == 0x7ffu) {
         flags |= special_flags(xh, xl, yh, yl);
         return;
     }
     const uint32_t A1 = (xh & 0xfffffu) | (ex ? 0x100000u : 0u);
-    const uint32_t B1 = (yh & 0xfffffu) | (ey ? 0x100000u : 0u);
+    const uint32_t B1 = SQUARE ? A1 : ((yh & 0xfffffu) | (ey ? 0x100000u : 0u));
     if ((A1 | xl) == 0u || (B1 | yl) == 0u) return;  // a zero product adds nothing
     const int pos = (int)max(ex, 1u) + (int)max(ey, 1u) - 2;
     // 106-bit significand product (A1:xl) * (B1:yl)
@@ -172,13 +181,13 @@ __device__ __forceinline__ void exact_add(Win<Q> &W, uint32_t &flags, unsigned l
     const unsigned long long m11 =
         (unsigned long long)A1 * B1 + (unsigned long long)((uint32_t)(m01 >> 32) + (uint32_t)(m10 >> 32));
     const uint32_t p0 = (uint32_t)m00, p1 = (uint32_t)m10, p2 = (uint32_t)m11, p3 = (uint32_t)(m11 >> 32);
-    const uint32_t m = (uint32_t)((int32_t)(xh ^ yh) >> 31);
+    const uint32_t m = SQUARE ? 0u : (uint32_t)((int32_t)(xh ^ yh) >> 31);
     const int L = pos >> 5;
     uint32_t u[5];
     shift5(p0, p1, p2, p3, (uint32_t)pos & 31u, u);
     int q = L - W.a;
     if ((unsigned)q < (unsigned)Q) {
-        win_place_add<Q>(W, u, q, m);
+        win_place_add<Q, !SQUARE>(W, u, q, m);
         return;
     }
     if (W.a < 0 || q >= Q) {
@@ -188,7 +197,7 @@ __device__ __forceinline__ void exact_add(Win<Q> &W, uint32_t &flags, unsigned l
         int a = L - (Q >= 2 ? Q - 2 : 0);
         a = a < 0 ? 0 : a;
         W.a = a;
-        win_place_add<Q>(W, u, L - a, m);
+        win_place_add<Q, !SQUARE>(W, u, L - a, m);
         return;
     }
     smem_deposit(sacc, u, L, m);
@@ -225,7 +234,7 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
     shift5(p0, p1, p2, p3, (uint32_t)pos & 31u, u);
     const int q = L - H.a;
     if ((unsigned)q < (unsigned)Q) {
-        win_place_add<Q>(H, u, q, m);
+        win_place_add<Q, true>(H, u, q, m);
         return;
     }
     const int back = Q >= 2 ? Q - 2 : 0;
@@ -237,18 +246,18 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
 #pragma unroll
         for (int k = 0; k < 8; k++) H.w[k] = 0u;
         H.a = L - back < 0 ? 0 : L - back;
-        win_place_add<Q>(H, u, L - H.a, m);
+        win_place_add<Q, true>(H, u, L - H.a, m);
         return;
     }
     const int ql = L - Lw.a;
     if ((unsigned)ql < (unsigned)Q) {
-        win_place_add<Q>(Lw, u, ql, m);
+        win_place_add<Q, true>(Lw, u, ql, m);
         return;
     }
     if (ql >= Q) {
         win_flush<Q>(Lw, sacc);
         Lw.a = L - back < 0 ? 0 : L - back;
-        win_place_add<Q>(Lw, u, L - Lw.a, m);
+        win_place_add<Q, true>(Lw, u, L - Lw.a, m);
         return;
     }
     smem_deposit(sacc, u, L, m);

@@ -123,27 +123,23 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
                     reinterpret_cast<const double *>(bufs + cur * SPMV_BUF + SPMV_CAP * sizeof(int32_t));
                 const int lo = (int)(b0 - c0.B), hi = (int)(e0 - c0.B);
                 for (int k0 = lo; k0 < hi; k0 += 8) {
-                    double xv[8], av[8];
-                    bool use[8];
+                    // all gathers first (up to 8 in flight), then the chain in
+                    // stored order; values and indices are re-read from shared
+                    // memory so only the gathered x stay in registers
+                    double xv[8];
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
-                        use[j] = false;
                         xv[j] = 0.0;
-                        av[j] = 0.0;
                         if (k0 + j < hi) {
                             const int32_t cidx = scol[k0 + j];
-                            av[j] = sval[k0 + j];
-                            if ((uint64_t)(int64_t)cidx < (uint64_t)A.n) {
-                                xv[j] = __ldg(x + cidx);
-                                use[j] = true;
-                            } else {
-                                bad = true;
-                            }
+                            if ((uint64_t)(int64_t)cidx < (uint64_t)A.n) xv[j] = __ldg(x + cidx);
+                            else bad = true;
                         }
                     }
 #pragma unroll
                     for (int j = 0; j < 8; j++)
-                        if (use[j]) acc = fma(av[j], xv[j], acc);
+                        if (k0 + j < hi && (uint64_t)(int64_t)scol[k0 + j] < (uint64_t)A.n)
+                            acc = fma(sval[k0 + j], xv[j], acc);
                 }
             } else {
                 acc = spmv_row(A, r, x, bad);

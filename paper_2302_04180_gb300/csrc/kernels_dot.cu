@@ -141,6 +141,16 @@ static CSRView view(const CSRArgs &A) { return CSRView{A.n, A.nnz, A.rowptr, A.c
 
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s) {
+    static int applied[64] = {-2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2,
+                              -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2,
+                              -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2,
+                              -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && applied[dev] != cfg.carveout) {
+        cudaFuncSetAttribute(k_spmv, cudaFuncAttributePreferredSharedMemoryCarveout, cfg.carveout);
+        cudaGetLastError();
+        applied[dev] = cfg.carveout;
+    }
     k_spmv<<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
     return cudaGetLastError();
 }

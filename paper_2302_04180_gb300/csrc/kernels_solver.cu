@@ -20,6 +20,7 @@
 // Once the stop flag is set, every later kernel returns at once.
 #include "kernels.cuh"
 #include "launch.h"
+#include "tails.cuh"
 
 namespace rbs {
 
@@ -37,159 +38,6 @@ struct Ctx {
     unsigned *err;
     int spmv_mode;
 };
-
-// ---- scalar tails (one thread of the last block) ------------------------------
-
-__device__ __forceinline__ void rec_begin(SolverState *st) {
-    for (int f = 0; f < RBS_HIST_W; f++) st->rec[f] = qnan();
-}
-__device__ __forceinline__ void rec_commit(SolverState *st, double *hist) {
-    const int j = st->iter - 1;
-    if (j >= 0 && j < st->hist_cap)
-        for (int f = 0; f < RBS_HIST_W; f++) hist[(int64_t)j * RBS_HIST_W + f] = st->rec[f];
-}
-__device__ __forceinline__ void stop(SolverState *st, int status) {
-    st->status = status;
-    st->done = 1;
-}
-
-// set-up, classic: rho = <r0,r0>, tau0 = sqrt(rho), tau_max = tol * tau0
-__device__ void tail_cls_setup(SolverState *st, const double *v) {
-    const double rho = v[0];
-    const double tau = __dsqrt_rn(rho);
-    st->rho = rho;
-    st->rho0 = rho;
-    st->tau = tau;
-    st->tau0 = tau;
-    st->tau_max = __dmul_rn(st->tol, tau);
-    st->iter = 0;
-    st->status = RBS_OK;
-    st->done = 0;
-    if (!finite_d(tau)) stop(st, RBS_ENAN);
-    else if (!(tau > st->tau_max) || st->maxit <= 0) st->done = 1;
-}
-
-// S3: alpha = rho / <r0, s>
-__device__ void tail_cls_alpha(SolverState *st, const double *v) {
-    rec_begin(st);
-    const double sigma = v[0];
-    st->rec[0] = sigma;
-    if (sigma == 0.0) { stop(st, RBS_EBREAKDOWN); return; }
-    const double alpha = __ddiv_rn(st->rho, sigma);
-    st->rec[1] = alpha;
-    if (!finite_d(alpha)) { stop(st, RBS_ENAN); return; }
-    st->alpha = alpha;
-}
-
-// S7: omega = <q,y> / <y,y> (0 when y == 0)
-__device__ void tail_cls_omega(SolverState *st, const double *v) {
-    const double gamma = v[0], delta = v[1];
-    const double omega = (delta == 0.0) ? 0.0 : __ddiv_rn(gamma, delta);
-    st->rec[2] = gamma;
-    st->rec[3] = delta;
-    st->rec[4] = omega;
-    st->omega = omega;
-}
-
-// S10, S11 and the while test
-__device__ void tail_cls_beta(SolverState *st, const double *v, double *hist) {
-    const double rho1 = v[0], theta = v[1];
-    const double tau = __dsqrt_rn(theta);
-    st->rec[5] = rho1;
-    st->rec[6] = theta;
-    st->rec[7] = tau;
-    st->iter += 1;
-    st->tau = tau;
-    const double gamma = st->rec[2], delta = st->rec[3], omega = st->omega;
-    if (!finite_d(gamma) || !finite_d(delta) || !finite_d(omega) || !finite_d(rho1) || !finite_d(theta) ||
-        !finite_d(tau)) {
-        rec_commit(st, hist);
-        stop(st, RBS_ENAN);
-        return;
-    }
-    if (!(tau > st->tau_max)) { rec_commit(st, hist); st->done = 1; return; }
-    if (omega == 0.0 || rho1 == 0.0) { rec_commit(st, hist); stop(st, RBS_EBREAKDOWN); return; }
-    const double beta = __dmul_rn(__ddiv_rn(rho1, st->rho), __ddiv_rn(st->alpha, omega));
-    st->rec[8] = beta;
-    rec_commit(st, hist);
-    if (!finite_d(beta)) { stop(st, RBS_ENAN); return; }
-    st->beta = beta;
-    st->rho = rho1;
-    if (st->iter >= st->maxit) st->done = 1;
-}
-
-// set-up, pipelined: rho = <r0,r0>, mu = <r0,w0>, alpha0 = rho / mu
-__device__ void tail_pipe_setup(SolverState *st, const double *v) {
-    const double rho = v[0], mu = v[1];
-    const double tau = __dsqrt_rn(rho);
-    st->rho = rho;
-    st->rho0 = rho;
-    st->mu0 = mu;
-    st->tau = tau;
-    st->tau0 = tau;
-    st->tau_max = __dmul_rn(st->tol, tau);
-    st->alpha0 = qnan();
-    st->beta = 0.0;
-    st->omega = 0.0;
-    st->iter = 0;
-    st->status = RBS_OK;
-    st->done = 0;
-    if (!finite_d(tau) || !finite_d(mu)) { stop(st, RBS_ENAN); return; }
-    if (!(tau > st->tau_max) || st->maxit <= 0) { st->done = 1; return; }
-    if (mu == 0.0) { stop(st, RBS_EBREAKDOWN); return; }
-    const double alpha = __ddiv_rn(rho, mu);
-    st->alpha = alpha;
-    st->alpha0 = alpha;
-    if (!finite_d(alpha)) stop(st, RBS_ENAN);
-}
-
-// S8 + S11: omega = <q,y> / <y,y>
-__device__ void tail_pipe_omega(SolverState *st, const double *v) {
-    rec_begin(st);
-    const double gamma = v[0], delta = v[1];
-    const double omega = (delta == 0.0) ? 0.0 : __ddiv_rn(gamma, delta);
-    st->rec[0] = gamma;
-    st->rec[1] = delta;
-    st->rec[2] = omega;
-    st->omega = omega;
-}
-
-// S16 + S19 and the while test
-__device__ void tail_pipe_beta(SolverState *st, const double *v, double *hist) {
-    const double rho1 = v[0], a = v[1], c = v[2], e = v[3], theta = v[4];
-    const double tau = __dsqrt_rn(theta);
-    st->rec[3] = rho1;
-    st->rec[4] = a;
-    st->rec[5] = c;
-    st->rec[6] = e;
-    st->rec[7] = theta;
-    st->rec[8] = tau;
-    st->iter += 1;
-    st->tau = tau;
-    const double gamma = st->rec[0], delta = st->rec[1], omega = st->omega;
-    if (!finite_d(gamma) || !finite_d(delta) || !finite_d(omega) || !finite_d(rho1) || !finite_d(a) ||
-        !finite_d(c) || !finite_d(e) || !finite_d(theta) || !finite_d(tau)) {
-        rec_commit(st, hist);
-        stop(st, RBS_ENAN);
-        return;
-    }
-    if (!(tau > st->tau_max)) { rec_commit(st, hist); st->done = 1; return; }
-    if (omega == 0.0 || rho1 == 0.0) { rec_commit(st, hist); stop(st, RBS_EBREAKDOWN); return; }
-    const double beta = __dmul_rn(__ddiv_rn(rho1, st->rho), __ddiv_rn(st->alpha, omega));
-    const double bw = __dmul_rn(beta, omega);
-    const double den = fma(-bw, e, fma(beta, c, a));
-    st->rec[9] = beta;
-    st->rec[10] = den;
-    if (den == 0.0) { rec_commit(st, hist); stop(st, RBS_EBREAKDOWN); return; }
-    const double alpha = __ddiv_rn(rho1, den);
-    st->rec[11] = alpha;
-    rec_commit(st, hist);
-    if (!finite_d(beta) || !finite_d(den) || !finite_d(alpha)) { stop(st, RBS_ENAN); return; }
-    st->beta = beta;
-    st->alpha = alpha;
-    st->rho = rho1;
-    if (st->iter >= st->maxit) st->done = 1;
-}
 
 // ---- classic kernels -------------------------------------------------------------
 
@@ -213,7 +61,7 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
         c.r0[i] = ri;
         c.p[i] = ri;
         c.ph[i] = __dmul_rn(ri, c.invd[i]);
-        red.add(0, ri, ri);
+        red.add_sq(0, ri);
     }
     if (bad) atomicOr(c.err, 1u);
     __shared__ double vals[R::K];
@@ -222,7 +70,7 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
 
 // K1: s = A phat, <r0, s>
 template <class R>
-__global__ void __launch_bounds__(256, 3) k_cls_k1(Ctx c) {
+__global__ void __launch_bounds__(256, 4) k_cls_k1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
@@ -260,7 +108,7 @@ __global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
 
 // K3: y = A qhat, <q, y>, <y, y>
 template <class R>
-__global__ void __launch_bounds__(256, 3) k_cls_k3(Ctx c) {
+__global__ void __launch_bounds__(256, 4) k_cls_k3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
@@ -268,7 +116,7 @@ __global__ void __launch_bounds__(256, 3) k_cls_k3(Ctx c) {
     spmv_each(c.A, c.qh, c.spmv_mode, bad, [&](int64_t i, double yi) {
         c.y[i] = yi;
         red.add(0, c.q[i], yi);
-        red.add(1, yi, yi);
+        red.add_sq(1, yi);
     });
     if (bad) atomicOr(c.err, 1u);
     __shared__ double vals[R::K];
@@ -295,14 +143,14 @@ __global__ void __launch_bounds__(256) k_cls_k4(Ctx c) {
             st2(c.r, i, r);
             red.add(0, r0.x, r.x);
             red.add(0, r0.y, r.y);
-            red.add(1, r.x, r.x);
-            red.add(1, r.y, r.y);
+            red.add_sq(1, r.x);
+            red.add_sq(1, r.y);
         } else {
             c.x[i] = fma(om, c.qh[i], fma(al, c.ph[i], c.x[i]));
             const double r = fma(nom, c.y[i], c.q[i]);
             c.r[i] = r;
             red.add(0, c.r0[i], r);
-            red.add(1, r, r);
+            red.add_sq(1, r);
         }
     });
     __shared__ double vals[R::K];
@@ -363,7 +211,7 @@ __global__ void __launch_bounds__(256) k_pipe_setup2(Ctx c) {
         c.w[i] = wi;
         c.wh[i] = __dmul_rn(wi, c.invd[i]);
         const double r0 = c.r0[i];
-        red.add(0, r0, c.r[i]);
+        red.add_sq(0, r0);  // r = r0 at set-up
         red.add(1, r0, wi);
     });
     if (bad) atomicOr(c.err, 1u);
@@ -407,7 +255,7 @@ __global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
         c.y[i] = y;
         c.zh[i] = __dmul_rn(z, c.invd[i]);
         red.add(0, q, y);
-        red.add(1, y, y);
+        red.add_sq(1, y);
     }
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_omega(c.st, vals);
@@ -435,7 +283,7 @@ __global__ void __launch_bounds__(256) k_pipe_p3(Ctx c) {
         red.add(1, r0, w);
         red.add(2, r0, c.s[i]);
         red.add(3, r0, c.z[i]);
-        red.add(4, r, r);
+        red.add_sq(4, r);
     }
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_beta(c.st, vals, c.hist);
@@ -494,7 +342,38 @@ static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, Kern
     return cudaGetLastError();
 }
 
+// Shared-memory carveout (percent of the unified L1/shared storage, -1 = the
+// driver's choice) of the kernels that stage data per warp. The x gathers of
+// the SpMV live on L1 hits, so the split is a tuning knob, not a maximum.
+template <class R1, class R2, class R5>
+static void prefer_shared(int c) {
+    cudaFuncSetAttribute(k_cls_k1<R1>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_cls_k3<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_cls_k4<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_pipe_setup2<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_pipe_p1<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_pipe_p3<R5>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaGetLastError();
+}
+
 cudaError_t solver_setup(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t) {
+    static int applied_exact[64], applied_plain[64];
+    static bool init = false;
+    if (!init) {
+        for (int i = 0; i < 64; i++) applied_exact[i] = applied_plain[i] = -2;
+        init = true;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        const int c = a.carveout;
+        if (a.dot_mode == RBS_DOT_PLAIN && applied_plain[dev] != c) {
+            prefer_shared<PlainR<1>, PlainR<2>, PlainR<5>>(c);
+            applied_plain[dev] = c;
+        } else if (a.dot_mode != RBS_DOT_PLAIN && applied_exact[dev] != c) {
+            prefer_shared<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(c);
+            applied_exact[dev] = c;
+        }
+    }
     if (a.dot_mode == RBS_DOT_PLAIN) return setup_t<PlainR<1>, PlainR<2>, PlainR<5>>(a, variant, s, t);
     return setup_t<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(a, variant, s, t);
 }

@@ -22,7 +22,8 @@ struct CSRArgs {
 struct Cfg {
     int grid = 0;
     int block = 256;
-    int mode = 0;  // SpMV row schedule: 0 warp-staged, 1 thread per row
+    int mode = 0;       // SpMV row schedule: 0 warp-staged, 1 thread per row
+    int carveout = -1;  // shared-memory carveout percent, -1 = driver default
 };
 
 // Set the calling thread's rbs_last_error() message and return `code`.
@@ -57,6 +58,7 @@ struct SolverArgs {
     double *hist;
     unsigned *err;
     int dot_mode;
+    int carveout;  // shared-memory carveout percent for staging kernels, -1 = driver default
     Cfg vec, spmv;
 };
 

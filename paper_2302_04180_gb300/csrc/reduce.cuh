@@ -34,6 +34,9 @@ struct ExactR {
     __device__ __forceinline__ void add(int k, double x, double y) {
         exact_add<Q>(win[k], flags[k], sacc[k], x, y);
     }
+    __device__ __forceinline__ void add_sq(int k, double x) {
+        exact_add<Q, true>(win[k], flags[k], sacc[k], x, x);
+    }
     // true in the last block, with vals[0..K-1] rounded (shared memory)
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
         return exact_finish<K, Q>(win, flags, sacc, sflags, g, vals);
@@ -86,6 +89,7 @@ struct PlainR {
         for (int k = 0; k < K; k++) s[k] = 0.0;
     }
     __device__ __forceinline__ void add(int k, double x, double y) { s[k] = fma(x, y, s[k]); }
+    __device__ __forceinline__ void add_sq(int k, double x) { s[k] = fma(x, x, s[k]); }
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
         __shared__ double s_part[K][32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -23,6 +23,7 @@ def rbs(dev):
     yield m
     for k in ("vec.grid", "vec.block", "spmv.block", "spmv.mode", "solve.check_every"):
         m.rbs_set_param(k, 0)
+    m.rbs_set_param("smem.carveout", 75)
 
 
 def _gpu_solve(rbs, dev, A, tol, maxit, variant, b=None, **kw):
@@ -86,9 +87,11 @@ def test_x0_and_given_diagonal(rbs, dev, orc, variant):
 def test_launch_shape_and_chunk_independence(rbs, dev, orc):
     A = gen.convdiff3d(14, 10.0)
     o = orc.solve(A, orc.spmv(A, np.ones(A.n)), tol=1e-10, maxit=500, variant=0)
-    for vg, vb, sb, ce, lm, sm in ((0, 0, 0, 0, 0, 0), (0, 0, 0, 0, 1, 1), (1, 32, 32, 1, 1, 0),
-                                   (7, 128, 64, 3, 0, 1), (500, 256, 256, 50, 1, 0), (152, 64, 128, 0, 0, 1)):
+    for vg, vb, sb, ce, lm, sm, co in ((0, 0, 0, 0, 0, 0, 75), (0, 0, 0, 0, 1, 1, -1), (1, 32, 32, 1, 1, 0, 100),
+                                       (7, 128, 64, 3, 0, 1, 50), (500, 256, 256, 50, 1, 0, 0),
+                                       (152, 64, 128, 0, 0, 1, 75)):
         rbs.rbs_set_param("spmv.mode", sm)
+        rbs.rbs_set_param("smem.carveout", co)
         rbs.rbs_set_param("vec.grid", vg)
         rbs.rbs_set_param("vec.block", vb)
         rbs.rbs_set_param("spmv.block", sb)
@@ -99,6 +102,7 @@ def test_launch_shape_and_chunk_independence(rbs, dev, orc):
             _assert_same_run(g, ov)
     for k in ("vec.grid", "vec.block", "spmv.block", "spmv.mode"):
         rbs.rbs_set_param(k, 0)
+    rbs.rbs_set_param("smem.carveout", 75)
 
 
 def test_run_to_run_bitwise(rbs, dev):
