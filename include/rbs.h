@@ -216,6 +216,30 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0,
                  const rbs_opts *opts, double *x_out, rbs_info *info, rbs_history *hist,
                  rbs_prof *prof, void *stream);
 
+/* ---- batched solves ----------------------------------------------------------------
+ * Many independent systems (each as in rbs_solve, Fig. 2 or Fig. 4 per system)
+ * in one persistent launch: thread-block clusters of 8 CTAs take systems from a
+ * queue, largest first, and run each solve to completion. Every system's
+ * iterates, history and x are bitwise those rbs_solve gives for it alone, in any
+ * batch. All pointers of an rbs_system are device memory; x0 and jacobi_diag
+ * may be NULL. systems, infos (nsys each) and hists (nsys, nullable; a record
+ * with cap == 0 keeps no history) are host arrays. Synchronises the stream.
+ * Returns RBS_EINVAL if any system fails the argument or structure checks
+ * (those systems report status RBS_EINVAL and are not solved; the others are),
+ * else RBS_OK; per-system breakdowns are in infos[i].status. */
+typedef struct {
+    rbs_csr A;
+    const double *b;
+    const double *x0;
+    const double *jacobi_diag;
+    double *x;
+    double tol;
+    int32_t maxit;
+    int32_t variant;
+} rbs_system;
+int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                      void *stream);
+
 /* ---- library control ---------------------------------------------------------- */
 /* Synchronise `stream`, then return and clear the workspace error word:
  * RBS_OK, or RBS_EINVAL if a kernel met an out-of-range CSR index. */

@@ -35,7 +35,7 @@ PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv")
 # every symbol include/rbs.h declares
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
            "rbs_spmv_csr", "rbs_jacobi_invd", "rbs_jacobi_apply", "rbs_solve",
-           "rbs_solve_ex", "rbs_stream_status", "rbs_release", "rbs_set_param",
+           "rbs_solve_ex", "rbs_solve_batched", "rbs_stream_status", "rbs_release", "rbs_set_param",
            "rbs_get_param", "rbs_last_error", "rbs_version")
 
 
@@ -60,6 +60,11 @@ class _Info(C.Structure):
                 ("reserved", C.c_int32), ("tau0", C.c_double), ("tau_final", C.c_double),
                 ("rho0", C.c_double), ("tau_max", C.c_double), ("alpha0", C.c_double),
                 ("mu0", C.c_double)]
+
+
+class _System(C.Structure):
+    _fields_ = [("A", _Csr), ("b", C.c_void_p), ("x0", C.c_void_p), ("jacobi_diag", C.c_void_p),
+                ("x", C.c_void_p), ("tol", C.c_double), ("maxit", C.c_int32), ("variant", C.c_int32)]
 
 
 class _Hist(C.Structure):
@@ -99,6 +104,7 @@ def load(path: str | None = None):
                           C.POINTER(_Hist), vp],
             "rbs_solve_ex": [C.POINTER(_Csr), vp, vp, vp, dbl, i32, i32, C.POINTER(_Opts), vp,
                              C.POINTER(_Info), C.POINTER(_Hist), C.POINTER(_Prof), vp],
+            "rbs_solve_batched": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist), vp],
             "rbs_stream_status": [vp],
             "rbs_release": [],
             "rbs_set_param": [C.c_char_p, i64],
@@ -309,3 +315,37 @@ def rbs_solve(A, b, x0=None, jacobi_diag=None, tol=1e-8, maxit=1000, variant=RBS
         "prof": {PROF_KIND_NAMES[k]: (int(prof.launches[k]), float(prof.ms[k]))
                  for k in range(len(PROF_KIND_NAMES))} if profile else None,
     }
+
+
+def rbs_solve_batched(systems, history=True, stream=None):
+    """Solve many independent systems in one persistent launch. `systems` is a
+    list of dicts with keys A (DeviceCSR), b, x (device tensors), and optional
+    x0, jacobi_diag, tol (1e-8), maxit (1000), variant (0). Returns a list of
+    per-system dicts like rbs_solve's (x is the caller's tensor)."""
+    nsys = len(systems)
+    arr = (_System * nsys)()
+    infos = (_Info * nsys)()
+    hists = (_Hist * nsys)()
+    recs = []
+    for i, sd in enumerate(systems):
+        A = sd["A"]
+        arr[i] = _System(_csr(A), _ptr(sd["b"]), _ptr(sd.get("x0")), _ptr(sd.get("jacobi_diag")),
+                         _ptr(sd["x"]), float(sd.get("tol", 1e-8)), int(sd.get("maxit", 1000)),
+                         int(sd.get("variant", RBS_CLASSIC)))
+        cap = max(int(sd.get("maxit", 1000)), 1) if history else 0
+        rec = np.empty((max(cap, 1), RBS_HIST_W), dtype=np.float64)
+        recs.append(rec)
+        hists[i] = _Hist(cap, 0, rec.ctypes.data)
+    first = systems[0]["b"] if nsys else None
+    rc = load().rbs_solve_batched(nsys, arr, infos, hists if history else None,
+                                  _stream(stream, first))
+    if rc not in (RBS_OK, RBS_EINVAL):
+        _check(rc)
+    out = []
+    for i in range(nsys):
+        I = infos[i]
+        out.append({"x": systems[i]["x"], "iters": I.iters, "converged": I.converged,
+                    "status": I.status, "tau0": I.tau0, "tau_final": I.tau_final, "rho0": I.rho0,
+                    "tau_max": I.tau_max, "alpha0": I.alpha0, "mu0": I.mu0,
+                    "hist": recs[i][: hists[i].len].copy() if history else None})
+    return out

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/rbs.h): argument checks, the
 // per-(device, stream) workspace, host/device staging, and the solver driver
 // that enqueues iterations and watches the device-resident stop flag.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -89,6 +90,7 @@ struct Workspace {
     double *d_out = nullptr;
     unsigned *h_err = nullptr;
     Buf vec, hist, stage[8];
+    Buf batch_work, batch_hist, batch_sys, batch_order, batch_out, batch_queue;
     std::vector<cudaEvent_t> evpool;
     std::vector<cudaEvent_t> ev_chunk;
     // graph loop: one iteration captured as the body of a conditional WHILE node
@@ -147,6 +149,9 @@ void ws_free(Workspace *w) {
     cudaFreeHost(w->h_err);
     cudaFree(w->vec.p);
     cudaFree(w->hist.p);
+    for (Buf *b : {&w->batch_work, &w->batch_hist, &w->batch_sys, &w->batch_order, &w->batch_out,
+                   &w->batch_queue})
+        cudaFree(b->p);
     for (auto &b : w->stage) cudaFree(b.p);
     for (auto e : w->evpool) cudaEventDestroy(e);
     for (auto e : w->ev_chunk) cudaEventDestroy(e);
@@ -668,3 +673,117 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
 }
 
 }  // extern "C"
+
+extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                                 void *stream) {
+    if (nsys < 0 || (nsys > 0 && (!systems || !infos))) return fail(RBS_EINVAL, "bad batch arguments");
+    if (nsys == 0) return RBS_OK;
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    std::vector<BatchSys> sys((size_t)nsys);
+    std::vector<char> valid((size_t)nsys, 1);
+    size_t work_elems = 0, hist_recs = 0;
+    for (int i = 0; i < nsys; i++) {
+        const rbs_system &S = systems[i];
+        memset(&infos[i], 0, sizeof infos[i]);
+        bool ok = S.A.n > 0 && S.A.n <= 0x7fffffff && S.A.nnz >= 0 && S.A.rowptr &&
+                  (S.A.nnz == 0 || (S.A.col && S.A.val)) && S.b && S.x && S.maxit >= 0 && S.tol >= 0.0 &&
+                  (S.variant == RBS_CLASSIC || S.variant == RBS_PIPELINED);
+        ok = ok && is_device_ptr(S.A.rowptr) && is_device_ptr(S.b) && is_device_ptr(S.x) &&
+             (S.A.nnz == 0 || (is_device_ptr(S.A.col) && is_device_ptr(S.A.val))) &&
+             (!S.x0 || is_device_ptr(S.x0)) && (!S.jacobi_diag || is_device_ptr(S.jacobi_diag));
+        if (hists && (hists[i].cap < 0 || (hists[i].cap > 0 && !hists[i].rec))) ok = false;
+        valid[(size_t)i] = ok;
+        if (!ok) continue;
+        const int64_t stride = (S.A.n + 31) / 32 * 32;
+        work_elems += (size_t)stride * (S.variant == RBS_PIPELINED ? 17 : 9);
+        const int cap = hists ? std::min(hists[i].cap, S.maxit) : 0;
+        hist_recs += (size_t)(cap > 0 ? cap : 0);
+    }
+    CK(ensure(w->batch_work, work_elems * 8));
+    CK(ensure(w->batch_hist, (hist_recs > 0 ? hist_recs : 1) * RBS_HIST_W * 8));
+    CK(ensure(w->batch_sys, (size_t)nsys * sizeof(BatchSys)));
+    CK(ensure(w->batch_order, (size_t)nsys * sizeof(int32_t)));
+    CK(ensure(w->batch_out, (size_t)nsys * sizeof(BatchOut)));
+    CK(ensure(w->batch_queue, 16));
+    size_t woff = 0, hoff = 0;
+    std::vector<int32_t> order;
+    for (int i = 0; i < nsys; i++) {
+        BatchSys &B = sys[(size_t)i];
+        memset(&B, 0, sizeof B);
+        if (!valid[(size_t)i]) continue;
+        const rbs_system &S = systems[i];
+        B.A = CSRArgs{S.A.n, S.A.nnz, S.A.rowptr, S.A.col, S.A.val};
+        B.b = S.b;
+        B.x0 = S.x0;
+        B.diag = S.jacobi_diag;
+        B.x = S.x;
+        B.stride = (S.A.n + 31) / 32 * 32;
+        B.work = (double *)w->batch_work.p + woff;
+        woff += (size_t)B.stride * (S.variant == RBS_PIPELINED ? 17 : 9);
+        B.tol = S.tol;
+        B.maxit = S.maxit;
+        B.variant = S.variant;
+        const int cap = hists ? std::min(hists[i].cap, S.maxit) : 0;
+        B.hist_cap = cap > 0 ? cap : 0;
+        B.hist = B.hist_cap ? (double *)w->batch_hist.p + hoff * RBS_HIST_W : nullptr;
+        hoff += (size_t)B.hist_cap;
+        order.push_back(i);
+    }
+    // largest systems first (then by index, so the order is deterministic)
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return systems[a].A.nnz + systems[a].A.n > systems[b].A.nnz + systems[b].A.n;
+    });
+    const int nq = (int)order.size();
+    CK(cudaMemcpyAsync(w->batch_sys.p, sys.data(), (size_t)nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
+                       w->stream));
+    if (nq > 0)
+        CK(cudaMemcpyAsync(w->batch_order.p, order.data(), (size_t)nq * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           w->stream));
+    CK(cudaMemsetAsync(w->batch_out.p, 0, (size_t)nsys * sizeof(BatchOut), w->stream));
+    CK(cudaMemsetAsync(w->batch_queue.p, 0, 16, w->stream));
+    if (nq > 0) {
+        // structure check and Jacobi set-up of the valid systems, then the solves
+        std::vector<BatchSys> packed;
+        packed.reserve((size_t)nq);
+        CK(launch_batch_prepare((const BatchSys *)w->batch_sys.p, nsys, (BatchOut *)w->batch_out.p, w->stream));
+        const int clusters = std::max(1, std::min(batch_max_clusters(), nq));
+        CK(launch_batch((const BatchSys *)w->batch_sys.p, (const int32_t *)w->batch_order.p, nq,
+                        (unsigned *)w->batch_queue.p, (BatchOut *)w->batch_out.p, clusters, w->stream));
+    }
+    std::vector<BatchOut> out((size_t)nsys);
+    CK(cudaMemcpyAsync(out.data(), w->batch_out.p, (size_t)nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost,
+                       w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    int ret = RBS_OK;
+    hoff = 0;
+    for (int i = 0; i < nsys; i++) {
+        rbs_info &I = infos[i];
+        const BatchOut &O = out[(size_t)i];
+        if (!valid[(size_t)i] || O.err) {
+            I.status = RBS_EINVAL;
+            ret = RBS_EINVAL;
+            if (hists) hists[i].len = 0;
+            continue;
+        }
+        I.iters = O.iters;
+        I.converged = O.converged;
+        I.status = O.status;
+        I.tau0 = O.tau0;
+        I.tau_final = O.tau_final;
+        I.rho0 = O.rho0;
+        I.tau_max = O.tau_max;
+        I.alpha0 = systems[i].variant == RBS_PIPELINED ? O.alpha0 : __builtin_nan("");
+        I.mu0 = systems[i].variant == RBS_PIPELINED ? O.mu0 : 0.0;
+        if (hists) {
+            const BatchSys &B = sys[(size_t)i];
+            hists[i].len = std::min(O.iters, B.hist_cap);
+            if (hists[i].len > 0)
+                CK(cudaMemcpy(hists[i].rec, B.hist, (size_t)hists[i].len * RBS_HIST_W * 8, cudaMemcpyDeviceToHost));
+        }
+    }
+    if (ret) fail(ret, "one or more systems failed the argument or structure checks");
+    return ret;
+}

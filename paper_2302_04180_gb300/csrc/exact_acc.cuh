@@ -276,13 +276,16 @@ constexpr int WARP_SCRATCH = 6144;   // bytes of shared memory private to each w
 // Each warp's private slice of one shared buffer. Phases of a kernel that
 // stage data per warp (SpMV operands, then the window flush) reuse it; a warp
 // only ever touches its own slice, so no block barrier is needed between them.
+template <int BYTES = WARP_SCRATCH>
 __device__ __forceinline__ unsigned char *warp_scratch() {
-    __shared__ __align__(16) unsigned char buf[MAX_WARPS * WARP_SCRATCH];
-    return buf + (threadIdx.x >> 5) * WARP_SCRATCH;
+    __shared__ __align__(16) unsigned char buf[MAX_WARPS * BYTES];
+    return buf + (threadIdx.x >> 5) * BYTES;
 }
+constexpr int FLUSH_SCRATCH = 32 * 8 * 8 + 32 * 4;  // staging of warp_flush
 
-template <int Q>
+template <int Q, int SCRATCH = WARP_SCRATCH>
 __device__ __forceinline__ void warp_flush(Win<Q> &W, unsigned long long *sacc) {
+    static_assert(SCRATCH >= FLUSH_SCRATCH, "flush staging");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool has = W.a >= 0;
@@ -294,8 +297,8 @@ __device__ __forceinline__ void warp_flush(Win<Q> &W, unsigned long long *sacc) 
         return;
     }
     __syncwarp();
-    long long(*st)[8] = reinterpret_cast<long long(*)[8]>(warp_scratch());  // 2 KB
-    int *off = reinterpret_cast<int *>(warp_scratch() + 32 * 8 * 8);          // 128 B
+    long long(*st)[8] = reinterpret_cast<long long(*)[8]>(warp_scratch<SCRATCH>());  // 2 KB
+    int *off = reinterpret_cast<int *>(warp_scratch<SCRATCH>() + 32 * 8 * 8);        // 128 B
 #pragma unroll
     for (int k = 0; k < 7; k++) st[lane][k] = has ? (long long)W.w[k] : 0ll;
     st[lane][7] = has ? (long long)(int32_t)W.w[7] : 0ll;

@@ -1,0 +1,436 @@
+// Batched solver: many independent systems in one persistent launch.
+//
+// Thread-block clusters of BC CTAs take systems from a queue (largest first)
+// and run a whole classic (Fig. 2) or pipelined (Fig. 4) solve each: the
+// system's rows are split across the cluster's CTAs, element-wise steps touch
+// only a CTA's own rows, the SpMV gathers x from the whole vector, and every
+// exact dot is reduced across the cluster through distributed shared memory.
+// Each CTA rounds the cluster-summed integers itself and runs the same scalar
+// recurrence on the same bits, so all CTAs of a cluster take the same
+// decisions and meet the same cluster barriers; no CTA ever spins on a flag.
+// Arithmetic, fma forms and readings are those of the per-step kernels, so a
+// system's result is bitwise the one rbs_solve gives.
+#include <cooperative_groups.h>
+
+#include "kernels.cuh"
+#include "launch.h"
+#include "tails.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rbs {
+
+constexpr int BC = 8;  // CTAs per cluster
+constexpr int BQ = 4;  // exact-dot window placements
+
+enum Slot { S_R, S_R0, S_P, S_PH, S_S, S_Q, S_QH, S_Y, S_INVD, S_RH, S_W, S_WH, S_T, S_SH, S_Z, S_ZH, S_V };
+
+// y_i for row i, fma chain in stored order from +0.0 (as spmv_row), with x
+// read through L2: other CTAs of the cluster wrote it inside this kernel.
+__device__ __forceinline__ double spmv_row_l2(const CSRView &A, int64_t i, const double *x, bool &bad) {
+    const int64_t b = A.rowptr[i], e = A.rowptr[i + 1];
+    double acc = 0.0;
+    if (b < 0 || e < b || e > A.nnz) {
+        bad = true;
+        return acc;
+    }
+    for (int64_t k0 = b; k0 < e; k0 += 8) {
+        double xv[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            xv[j] = 0.0;
+            if (k0 + j < e) {
+                const int32_t c = A.col[k0 + j];
+                if ((uint64_t)(int64_t)c < (uint64_t)A.n) xv[j] = __ldcg(x + c);
+                else bad = true;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (k0 + j < e && (uint64_t)(int64_t)A.col[k0 + j] < (uint64_t)A.n)
+                acc = fma(A.val[k0 + j], xv[j], acc);
+    }
+    return acc;
+}
+
+struct ClusterRed {
+    unsigned long long (*acc)[NL];  // this CTA's accumulators (shared)
+    long long (*red)[NL];           // cluster sums (shared)
+    uint32_t *flags, *rflags;
+    double *vals;
+};
+
+// Reduce K exact dots across the cluster; afterwards vals[0..K-1] hold the
+// rounded dots in every CTA and the accumulators are zero again.
+template <int K>
+__device__ __forceinline__ void cluster_reduce(cg::cluster_group &cl, Win<BQ> (&win)[K], uint32_t (&fl)[K],
+                                               const ClusterRed &R) {
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        warp_flush<BQ, FLUSH_SCRATCH>(win[k], R.acc[k]);
+        if (fl[k]) atomicOr(&R.flags[k], fl[k]);
+        fl[k] = 0u;
+    }
+    cl.sync();
+    for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) {
+        long long sum = 0;
+        for (int r = 0; r < BC; r++)
+            sum += (long long)*cl.map_shared_rank(&R.acc[0][0] + idx, r);
+        (&R.red[0][0])[idx] = sum;
+    }
+    if (threadIdx.x < K) {
+        uint32_t f = 0u;
+        for (int r = 0; r < BC; r++) f |= *cl.map_shared_rank(R.flags + threadIdx.x, r);
+        R.rflags[threadIdx.x] = f;
+    }
+    cl.sync();
+    for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) (&R.acc[0][0])[idx] = 0ull;
+    if (threadIdx.x < K) {
+        R.flags[threadIdx.x] = 0u;
+        R.vals[threadIdx.x] = round_limbs_thread(R.red[threadIdx.x], R.rflags[threadIdx.x]);
+    }
+    __syncthreads();
+}
+
+struct SysView {
+    CSRView A;
+    int64_t n, lo, hi;
+    double *v[17];
+    double *x;
+    const double *b, *x0;
+    double *hist;
+};
+
+__device__ __forceinline__ void sys_view(const BatchSys &S, unsigned rank, SysView &V) {
+    V.A = CSRView{S.A.n, S.A.nnz, S.A.rowptr, S.A.col, S.A.val};
+    V.n = S.A.n;
+    V.lo = V.n * (int64_t)rank / BC;
+    V.hi = V.n * (int64_t)(rank + 1) / BC;
+    for (int k = 0; k < 17; k++) V.v[k] = S.work + (int64_t)k * S.stride;
+    V.x = S.x;
+    V.b = S.b;
+    V.x0 = S.x0;
+    V.hist = S.hist;
+}
+
+#define OWN_ROWS(i) for (int64_t i = V.lo + threadIdx.x; i < V.hi; i += blockDim.x)
+
+__device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverState *st, const ClusterRed &R,
+                              bool &bad) {
+    double *r = V.v[S_R], *r0 = V.v[S_R0], *p = V.v[S_P], *ph = V.v[S_PH], *s = V.v[S_S], *q = V.v[S_Q],
+           *qh = V.v[S_QH], *y = V.v[S_Y], *invd = V.v[S_INVD], *x = V.x;
+    Win<BQ> w1[1], w2[2];
+    uint32_t f1[1] = {0u}, f2[2] = {0u, 0u};
+    w1[0].init();
+    w2[0].init();
+    w2[1].init();
+    OWN_ROWS(i) {
+        double ri;
+        if (V.x0) {
+            ri = __dsub_rn(V.b[i], spmv_row_l2(V.A, i, V.x0, bad));
+            x[i] = V.x0[i];
+        } else {
+            ri = V.b[i];
+            x[i] = 0.0;
+        }
+        r[i] = ri;
+        r0[i] = ri;
+        p[i] = ri;
+        ph[i] = __dmul_rn(ri, invd[i]);
+        exact_add<BQ, true>(w1[0], f1[0], R.acc[0], ri, ri);
+    }
+    cluster_reduce<1>(cl, w1, f1, R);
+    if (threadIdx.x == 0) tail_cls_setup(st, R.vals);
+    __syncthreads();
+    for (int guard = 0; !st->done && guard <= st->maxit; guard++) {
+        OWN_ROWS(i) {  // K1
+            const double si = spmv_row_l2(V.A, i, ph, bad);
+            s[i] = si;
+            exact_add<BQ>(w1[0], f1[0], R.acc[0], r0[i], si);
+        }
+        cluster_reduce<1>(cl, w1, f1, R);
+        if (threadIdx.x == 0) tail_cls_alpha(st, R.vals);
+        __syncthreads();
+        if (st->done) break;
+        const double na = -st->alpha;
+        OWN_ROWS(i) {  // K2
+            const double qi = fma(na, s[i], r[i]);
+            q[i] = qi;
+            qh[i] = __dmul_rn(qi, invd[i]);
+        }
+        cl.sync();
+        OWN_ROWS(i) {  // K3
+            const double yi = spmv_row_l2(V.A, i, qh, bad);
+            y[i] = yi;
+            exact_add<BQ>(w2[0], f2[0], R.acc[0], q[i], yi);
+            exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
+        }
+        cluster_reduce<2>(cl, w2, f2, R);
+        if (threadIdx.x == 0) tail_cls_omega(st, R.vals);
+        __syncthreads();
+        const double al = st->alpha, om = st->omega, nom = -om;
+        OWN_ROWS(i) {  // K4
+            x[i] = fma(om, qh[i], fma(al, ph[i], x[i]));
+            const double ri = fma(nom, y[i], q[i]);
+            r[i] = ri;
+            exact_add<BQ>(w2[0], f2[0], R.acc[0], r0[i], ri);
+            exact_add<BQ, true>(w2[1], f2[1], R.acc[1], ri, ri);
+        }
+        cluster_reduce<2>(cl, w2, f2, R);
+        if (threadIdx.x == 0) tail_cls_beta(st, R.vals, V.hist);
+        __syncthreads();
+        if (st->done) break;
+        const double be = st->beta;
+        OWN_ROWS(i) {  // K5
+            const double pi = fma(be, fma(nom, s[i], p[i]), r[i]);
+            p[i] = pi;
+            ph[i] = __dmul_rn(pi, invd[i]);
+        }
+        cl.sync();
+    }
+}
+
+__device__ void solve_pipelined(cg::cluster_group &cl, const SysView &V, SolverState *st, const ClusterRed &R,
+                                bool &bad) {
+    double *r = V.v[S_R], *r0 = V.v[S_R0], *rh = V.v[S_RH], *w = V.v[S_W], *wh = V.v[S_WH], *t = V.v[S_T],
+           *ph = V.v[S_PH], *s = V.v[S_S], *sh = V.v[S_SH], *z = V.v[S_Z], *zh = V.v[S_ZH], *v = V.v[S_V],
+           *q = V.v[S_Q], *qh = V.v[S_QH], *y = V.v[S_Y], *invd = V.v[S_INVD], *x = V.x;
+    Win<BQ> w2[2], w5[5];
+    uint32_t f2[2] = {0u, 0u}, f5[5] = {0u, 0u, 0u, 0u, 0u};
+    for (int k = 0; k < 2; k++) w2[k].init();
+    for (int k = 0; k < 5; k++) w5[k].init();
+    OWN_ROWS(i) {
+        double ri;
+        if (V.x0) {
+            ri = __dsub_rn(V.b[i], spmv_row_l2(V.A, i, V.x0, bad));
+            x[i] = V.x0[i];
+        } else {
+            ri = V.b[i];
+            x[i] = 0.0;
+        }
+        r[i] = ri;
+        r0[i] = ri;
+        rh[i] = __dmul_rn(ri, invd[i]);
+    }
+    cl.sync();
+    OWN_ROWS(i) {
+        const double wi = spmv_row_l2(V.A, i, rh, bad);
+        w[i] = wi;
+        wh[i] = __dmul_rn(wi, invd[i]);
+        const double r0i = r0[i];
+        exact_add<BQ, true>(w2[0], f2[0], R.acc[0], r0i, r0i);
+        exact_add<BQ>(w2[1], f2[1], R.acc[1], r0i, wi);
+    }
+    cluster_reduce<2>(cl, w2, f2, R);
+    if (threadIdx.x == 0) tail_pipe_setup(st, R.vals);
+    __syncthreads();
+    if (!st->done) {
+        OWN_ROWS(i) t[i] = spmv_row_l2(V.A, i, wh, bad);
+        cl.sync();
+    }
+    for (int guard = 0; !st->done && guard <= st->maxit; guard++) {
+        const double al = st->alpha, nal = -al, be = st->beta, nom = -st->omega;
+        const bool first = st->iter == 0;
+        OWN_ROWS(i) {  // P1: S1-S7, S9
+            double phi, si, shi, zi;
+            const double rhi = rh[i], wi = w[i], whi = wh[i], ti = t[i];
+            if (first) {
+                phi = rhi;
+                si = wi;
+                shi = whi;
+                zi = ti;
+            } else {
+                const double ph0 = ph[i], s0 = s[i], sh0 = sh[i], z0 = z[i], zh0 = zh[i], v0 = v[i];
+                phi = fma(be, fma(nom, sh0, ph0), rhi);
+                si = fma(be, fma(nom, z0, s0), wi);
+                shi = fma(be, fma(nom, zh0, sh0), whi);
+                zi = fma(be, fma(nom, v0, z0), ti);
+            }
+            const double qi = fma(nal, si, r[i]);
+            const double qhi = fma(nal, shi, rhi);
+            const double yi = fma(nal, zi, wi);
+            ph[i] = phi;
+            s[i] = si;
+            sh[i] = shi;
+            z[i] = zi;
+            q[i] = qi;
+            qh[i] = qhi;
+            y[i] = yi;
+            zh[i] = __dmul_rn(zi, invd[i]);
+            exact_add<BQ>(w2[0], f2[0], R.acc[0], qi, yi);
+            exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
+        }
+        cluster_reduce<2>(cl, w2, f2, R);  // also orders zhat for P2's gathers
+        if (threadIdx.x == 0) tail_pipe_omega(st, R.vals);
+        __syncthreads();
+        OWN_ROWS(i) v[i] = spmv_row_l2(V.A, i, zh, bad);  // P2
+        cl.sync();
+        const double om = st->omega, nom2 = -om;
+        OWN_ROWS(i) {  // P3: S12-S15, S17
+            const double qhi = qh[i], yi = y[i], qi = q[i];
+            x[i] = fma(om, qhi, fma(al, ph[i], x[i]));
+            const double ri = fma(nom2, yi, qi);
+            const double rhi = fma(nom2, fma(nal, zh[i], wh[i]), qhi);
+            const double wi = fma(nom2, fma(nal, v[i], t[i]), yi);
+            r[i] = ri;
+            rh[i] = rhi;
+            w[i] = wi;
+            wh[i] = __dmul_rn(wi, invd[i]);
+            const double r0i = r0[i];
+            exact_add<BQ>(w5[0], f5[0], R.acc[0], r0i, ri);
+            exact_add<BQ>(w5[1], f5[1], R.acc[1], r0i, wi);
+            exact_add<BQ>(w5[2], f5[2], R.acc[2], r0i, s[i]);
+            exact_add<BQ>(w5[3], f5[3], R.acc[3], r0i, z[i]);
+            exact_add<BQ, true>(w5[4], f5[4], R.acc[4], ri, ri);
+        }
+        cluster_reduce<5>(cl, w5, f5, R);  // also orders what for P4's gathers
+        if (threadIdx.x == 0) tail_pipe_beta(st, R.vals, V.hist);
+        __syncthreads();
+        if (st->done) break;
+        OWN_ROWS(i) t[i] = spmv_row_l2(V.A, i, wh, bad);  // P4
+        cl.sync();
+    }
+}
+
+__global__ void __cluster_dims__(BC, 1, 1) __launch_bounds__(256)
+    k_batch(const BatchSys *__restrict__ sys, const int32_t *__restrict__ order, int nsys, unsigned *queue,
+            BatchOut *out) {
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned rank = cl.block_rank();
+    __shared__ int s_next;
+    __shared__ SolverState st;
+    __shared__ unsigned long long s_acc[5][NL];
+    __shared__ long long s_red[5][NL];
+    __shared__ uint32_t s_flags[5], s_rflags[5];
+    __shared__ double s_vals[5];
+    __shared__ int s_bad;
+    for (int idx = threadIdx.x; idx < 5 * NL; idx += blockDim.x) (&s_acc[0][0])[idx] = 0ull;
+    if (threadIdx.x < 5) s_flags[threadIdx.x] = 0u;
+    ClusterRed R{s_acc, s_red, s_flags, s_rflags, s_vals};
+    cl.sync();  // every CTA of the cluster runs before any shared memory is touched remotely
+    for (int guard = 0; guard <= nsys; guard++) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const int q = (int)atomicAdd(queue, 1u);
+            for (int r = 0; r < BC; r++) *cl.map_shared_rank(&s_next, r) = q;
+        }
+        cl.sync();
+        const int qi = s_next;
+        cl.sync();
+        if (qi >= nsys) break;
+        const int si = order[qi];
+        const BatchSys &S = sys[si];
+        if (out[si].err) continue;  // failed the structure check: same for every CTA
+        if (threadIdx.x == 0) {
+            memset(&st, 0, sizeof st);
+            st.tol = S.tol;
+            st.maxit = S.maxit;
+            st.variant = S.variant;
+            st.hist_cap = rank == 0 ? S.hist_cap : 0;
+            s_bad = 0;
+        }
+        __syncthreads();
+        SysView V;
+        sys_view(S, rank, V);
+        bool bad = false;
+        if (S.variant == RBS_PIPELINED) solve_pipelined(cl, V, &st, R, bad);
+        else solve_classic(cl, V, &st, R, bad);
+        if (bad) atomicOr(reinterpret_cast<unsigned *>(&s_bad), 1u);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_bad) atomicOr(&out[si].err, 1u);
+            if (rank == 0) {
+                BatchOut o = out[si];
+                o.iters = st.iter;
+                o.status = st.status;
+                o.converged = (st.status == RBS_OK && !(st.tau > st.tau_max)) ? 1 : 0;
+                o.tau0 = st.tau0;
+                o.tau_final = st.tau;
+                o.rho0 = st.rho0;
+                o.tau_max = st.tau_max;
+                o.alpha0 = st.alpha0;
+                o.mu0 = st.mu0;
+                out[si].iters = o.iters;
+                out[si].status = o.status;
+                out[si].converged = o.converged;
+                out[si].tau0 = o.tau0;
+                out[si].tau_final = o.tau_final;
+                out[si].rho0 = o.rho0;
+                out[si].tau_max = o.tau_max;
+                out[si].alpha0 = o.alpha0;
+                out[si].mu0 = o.mu0;
+            }
+        }
+    }
+}
+
+// Per-system structure check and Jacobi set-up: one block per system.
+__global__ void __launch_bounds__(256) k_batch_prepare(const BatchSys *__restrict__ sys, int nsys, BatchOut *out) {
+    const int si = blockIdx.x;
+    if (si >= nsys) return;
+    const BatchSys &S = sys[si];
+    const CSRView A{S.A.n, S.A.nnz, S.A.rowptr, S.A.col, S.A.val};
+    double *invd = S.work + (int64_t)S_INVD * S.stride;
+    bool bad = false, bad_diag = false;
+    if (threadIdx.x == 0 && (A.rowptr[0] != 0 || A.rowptr[A.n] != A.nnz)) bad = true;
+    for (int64_t i = threadIdx.x; i < A.n; i += blockDim.x) {
+        const int64_t b = A.rowptr[i], e = A.rowptr[i + 1];
+        double d = 0.0;
+        bool found = false;
+        if (b < 0 || e < b || e > A.nnz) {
+            bad = true;
+        } else {
+            for (int64_t k = b; k < e; k++) {
+                const int32_t c = A.col[k];
+                if ((uint64_t)(int64_t)c >= (uint64_t)A.n) bad = true;
+                else if (!found && c == i) {
+                    d = A.val[k];
+                    found = true;
+                }
+            }
+        }
+        if (S.diag) {
+            d = S.diag[i];
+            found = true;
+        }
+        if (!found || d == 0.0 || d != d) {
+            bad_diag = true;
+            invd[i] = 0.0;
+        } else {
+            invd[i] = __ddiv_rn(1.0, d);
+        }
+    }
+    if (bad) atomicOr(&out[si].err, 1u);
+    if (bad_diag) atomicOr(&out[si].err, 2u);
+}
+
+cudaError_t launch_batch_prepare(const BatchSys *d_sys, int nsys, BatchOut *d_out, cudaStream_t s) {
+    k_batch_prepare<<<nsys, 256, 0, s>>>(d_sys, nsys, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, int nsys, unsigned *d_queue,
+                         BatchOut *d_out, int clusters, cudaStream_t s) {
+    k_batch<<<clusters * BC, 256, 0, s>>>(d_sys, d_order, nsys, d_queue, d_out);
+    return cudaGetLastError();
+}
+
+int batch_max_clusters() {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(BC, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = BC;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_batch, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+}  // namespace rbs

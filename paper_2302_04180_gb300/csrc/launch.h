@@ -78,6 +78,28 @@ cudaError_t solver_iteration(const SolverArgs &a, int variant, cudaStream_t s, K
 // flag is clear, and at most maxit + 1 bodies in any case.
 cudaError_t launch_set_cond(cudaGraphConditionalHandle h, SolverState *st, cudaStream_t s);
 
+// ---- batched solver (kernels_batch.cu) ----
+struct BatchSys {
+    CSRArgs A;
+    const double *b, *x0, *diag;
+    double *x;       // solution (device)
+    double *work;    // 17 vector slots of `stride` doubles (9 for classic)
+    int64_t stride;  // elements per slot
+    double tol;
+    int32_t maxit, variant;
+    double *hist;    // device history records (hist_cap of them), may be null
+    int32_t hist_cap, pad;
+};
+struct BatchOut {
+    int32_t iters, converged, status;
+    unsigned err;  // bit 0 invalid CSR, bit 1 zero/NaN/missing diagonal
+    double tau0, tau_final, rho0, tau_max, alpha0, mu0;
+};
+cudaError_t launch_batch_prepare(const BatchSys *d_sys, int nsys, BatchOut *d_out, cudaStream_t s);
+cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, int nsys, unsigned *d_queue,
+                         BatchOut *d_out, int clusters, cudaStream_t s);
+int batch_max_clusters();
+
 // occupancy-derived persistent grid for the kernels of one kind
 int solver_blocks_per_sm(int variant, int dot_mode, int which);
 

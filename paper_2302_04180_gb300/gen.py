@@ -288,3 +288,32 @@ def ill_conditioned_dot(n: int, cond: float, seed: int):
     perm = np.argsort(splitmix64(s(13), n), kind="stable")
     exact = Fraction(u) * Fraction(v)
     return np.ascontiguousarray(x[perm]), np.ascontiguousarray(y[perm]), exact
+
+
+def batch_workload(count: int, seed: int, n_min: int = 1000, n_max: int = 300000):
+    """Independent nonsymmetric convection-diffusion systems for batched solves.
+
+    Per system (SplitMix64, stream per field): 2D 5-point or 3D 7-point with
+    probability 1/2; target size n drawn log-uniform in [n_min, n_max], grid side
+    round(n^(1/dim)) (at least 3); Peclet number uniform in [0, 50]; a random unit
+    velocity direction; classic or pipelined with probability 1/2. Returns a list
+    of (CSR, variant) pairs.
+    """
+    sid = lambda tag: stream_id(seed, 900 + tag)  # noqa: E731
+    u_dim = uniform(sid(1), count)
+    u_n = uniform(sid(2), count)
+    u_pe = uniform(sid(3), count)
+    u_var = uniform(sid(4), count)
+    dirs = uniform(sid(5), 3 * count).reshape(count, 3) * 2.0 - 1.0
+    out = []
+    for k in range(count):
+        dim = 2 if u_dim[k] < 0.5 else 3
+        n_target = float(np.exp(np.log(n_min) + u_n[k] * (np.log(n_max) - np.log(n_min))))
+        side = max(3, int(round(n_target ** (1.0 / dim))))
+        pe = 50.0 * float(u_pe[k])
+        d = dirs[k, :dim]
+        if not np.any(d):
+            d = np.ones(dim)
+        A = convdiff2d(side, pe, tuple(d)) if dim == 2 else convdiff3d(side, pe, tuple(d))
+        out.append((A, 1 if u_var[k] >= 0.5 else 0))
+    return out
