@@ -278,6 +278,7 @@ def run_gpu(args):
     pipelined = {"value": rq_["iters"] / tq_, "iters": rq_["iters"], "converged": rq_["converged"]}
 
     kernels = _kernel_micro(rbs, gen, dev)
+    batched = _batched(rbs, gen, dev)
     gpu_launches = sum(v[0] for v in prof_tot.values())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -286,7 +287,7 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
             "plain_comparator": {**plain, "repro_over_plain_time": plain["value"] / repro_one},
-            "pipelined": pipelined, "kernels": kernels}
+            "pipelined": pipelined, "kernels": kernels, "batched": batched}
     if args.cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(A, b.cpu().numpy())
     print(json.dumps(line), flush=True)
@@ -307,6 +308,29 @@ def _traffic():
     except Exception:
         pass
     return None
+
+
+def _batched(rbs, gen, dev):
+    """512 independent convection-diffusion systems (2D/3D, n 1k-300k, Pe 0-50,
+    classic/pipelined mix, tol 1e-8) in one persistent cluster launch."""
+    import torch
+    work = gen.batch_workload(512, seed=0)
+    systems = []
+    for A, v in work:
+        Ad = rbs.to_device(A, dev)
+        b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+        systems.append({"A": Ad, "b": b, "x": torch.empty(A.n, dtype=torch.float64, device=dev),
+                        "tol": 1e-8, "maxit": 5000, "variant": v})
+    rbs.rbs_solve_batched(systems, history=False)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    res = rbs.rbs_solve_batched(systems, history=False)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    its = sum(r["iters"] for r in res)
+    return {"systems": len(systems), "unknowns": int(sum(A.n for A, _ in work)),
+            "seconds": dt, "systems_per_s": len(systems) / dt, "iters_per_s": its / dt,
+            "total_iters": its, "converged": int(sum(r["converged"] for r in res))}
 
 
 def _kernel_micro(rbs, gen, dev):

@@ -317,3 +317,50 @@ def batch_workload(count: int, seed: int, n_min: int = 1000, n_max: int = 300000
         A = convdiff2d(side, pe, tuple(d)) if dim == 2 else convdiff3d(side, pe, tuple(d))
         out.append((A, 1 if u_var[k] >= 0.5 else 0))
     return out
+
+
+def stencil27(N: int, perturb: float = 1e-4) -> CSR:
+    """3D 27-point stencil on an N^3 grid, the 'e-type' unsymmetric model of the
+    paper's scalability study (Sec. 5.2): the 27-point Poisson matrix (26 on the
+    diagonal, -1 for each of the up to 26 neighbours), with every neighbour below
+    the central point (lower column index) perturbed to -(1 - perturb). Columns
+    ascending (lexicographic i + N j + N^2 k)."""
+    n = N ** 3
+    idx = np.arange(n, dtype=np.int64)
+    coord = [idx % N, (idx // N) % N, idx // (N * N)]
+    cols_list, vals_list, masks = [], [], []
+    for dk in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            for di in (-1, 0, 1):
+                off = di + N * dj + N * N * dk
+                msk = np.ones(n, dtype=bool)
+                for c, d in zip(coord, (di, dj, dk)):
+                    if d < 0:
+                        msk &= c > 0
+                    elif d > 0:
+                        msk &= c < N - 1
+                cols_list.append(np.where(msk, idx + off, 0).astype(np.int32))
+                if off == 0:
+                    vals_list.append(26.0)
+                elif off < 0:
+                    vals_list.append(-(1.0 - perturb))
+                else:
+                    vals_list.append(-1.0)
+                masks.append(msk)
+    return _stencil_csr(n, cols_list, vals_list, masks, f"stencil27_{N}")
+
+
+def banded(n: int, band: int, perturb: float = 1e-4) -> CSR:
+    """Band matrix with bandL = bandU = band (nnz = (2 band + 1) n away from the
+    edges), the stand-in for the paper's weak-scaling band matrices (Sec. 5.2):
+    -1 above the diagonal, -(1 - perturb) below it, and a diagonal of 2 band + 1
+    (strictly dominant)."""
+    idx = np.arange(n, dtype=np.int64)
+    cols_list, vals_list, masks = [], [], []
+    for off in range(-band, band + 1):
+        c = idx + off
+        msk = (c >= 0) & (c < n)
+        cols_list.append(np.where(msk, c, 0).astype(np.int32))
+        vals_list.append(float(2 * band + 1) if off == 0 else (-(1.0 - perturb) if off < 0 else -1.0))
+        masks.append(msk)
+    return _stencil_csr(n, cols_list, vals_list, masks, f"banded_{n}_{band}")
