@@ -99,6 +99,19 @@ int rbs_exdot_partial(const double *x, const double *y, int64_t n, int64_t *limb
 /* out = RN(value of the limb array) (host or device out; device limbs). */
 int rbs_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, void *stream);
 
+/* Lightweight FPE-8 dot (Sec. 3.2: floating-point expansions of size eight
+ * with early exit, and a check that warns when the condition number or the
+ * dynamic range is too large to keep every bit). Each thread accumulates
+ * TwoProd results (Alg. 2) in an expansion of at most eight binary64 terms with
+ * TwoSum cascades (Alg. 1); the expansions are merged exactly and rounded once
+ * (correct rounding, the role of NearSum in the paper). If a thread needs a
+ * ninth term, a TwoProd may be inexact (|x*y| < 2^-969) or a value is not
+ * finite, the call falls back to rbs_exdot and sets *fell_back = 1 (nullable).
+ * Either way out = rbs_exdot's value, bit for bit. x, y: host or device;
+ * out: host or device. Synchronises the stream. */
+int rbs_fpe_dot(const double *x, const double *y, int64_t n, double *out, int32_t *fell_back,
+                void *stream);
+
 /* Allocation-free variant of rbs_exdot_multi (the paper has no counterpart; it
  * is a deployment aid). For callers that cannot allocate when they call: code
  * running while a CUDA graph is captured, latency-critical loops that cannot

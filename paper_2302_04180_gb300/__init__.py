@@ -35,7 +35,7 @@ PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv")
 # every symbol include/rbs.h declares
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
            "rbs_spmv_csr", "rbs_jacobi_invd", "rbs_jacobi_apply", "rbs_solve",
-           "rbs_solve_ex", "rbs_solve_batched", "rbs_stream_status", "rbs_release", "rbs_set_param",
+           "rbs_solve_ex", "rbs_solve_batched", "rbs_fpe_dot", "rbs_stream_status", "rbs_release", "rbs_set_param",
            "rbs_get_param", "rbs_last_error", "rbs_version")
 
 
@@ -104,6 +104,7 @@ def load(path: str | None = None):
                           C.POINTER(_Hist), vp],
             "rbs_solve_ex": [C.POINTER(_Csr), vp, vp, vp, dbl, i32, i32, C.POINTER(_Opts), vp,
                              C.POINTER(_Info), C.POINTER(_Hist), C.POINTER(_Prof), vp],
+            "rbs_fpe_dot": [vp, vp, i64, vp, vp, vp],
             "rbs_solve_batched": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist), vp],
             "rbs_stream_status": [vp],
             "rbs_release": [],
@@ -222,6 +223,17 @@ def rbs_exdot_multi(xs, ys, out=None, stream=None):
         out = torch.empty(k, dtype=torch.float64, device=xs[0].device)
     _check(load().rbs_exdot_multi(k, xa, ya, n, _ptr(out), _stream(stream, xs[0], out)))
     return out
+
+
+def rbs_fpe_dot(x, y, stream=None):
+    """Lightweight FPE-8 dot: returns (value, fell_back). The value is always
+    the correctly rounded dot (the exact path is taken when the expansions
+    cannot hold every bit)."""
+    res = np.zeros(1, dtype=np.float64)
+    fb = C.c_int32(0)
+    _check(load().rbs_fpe_dot(_ptr(x), _ptr(y), int(x.shape[0]), res.ctypes.data, C.byref(fb),
+                              _stream(stream, x, y)))
+    return float(res[0]), bool(fb.value)
 
 
 def rbs_exdot_noalloc(xs, ys, out, stream=None):

@@ -787,3 +787,41 @@ extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_in
     if (ret) fail(ret, "one or more systems failed the argument or structure checks");
     return ret;
 }
+
+extern "C" int rbs_fpe_dot(const double *x, const double *y, int64_t n, double *out, int32_t *fell_back,
+                           void *stream) {
+    if (n < 0 || !out || (n > 0 && (!x || !y))) return fail(RBS_EINVAL, "bad argument");
+    if (fell_back) *fell_back = 0;
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(w->mu);
+        if (n == 0) {
+            if (is_device_ptr(out)) CK(cudaMemsetAsync(out, 0, sizeof(double), w->stream));
+            else *out = 0.0;
+            return RBS_OK;
+        }
+        const void *dx, *dy;
+        if ((rc = to_device(w, 0, x, (size_t)n * 8, &dx))) return rc;
+        if ((rc = to_device(w, 1, y, (size_t)n * 8, &dy))) return rc;
+        CK(cudaMemsetAsync(&w->g->err, 0, sizeof(unsigned), w->stream));
+        Cfg c = exdot_cfg(w, n);
+        CK(launch_fpe_dot((const double *)dx, (const double *)dy, n, w->g, w->d_out, &w->g->err, c, w->stream));
+        unsigned lost = 0;
+        if ((rc = read_err(w, &lost))) return rc;
+        if (!lost) {
+            if (is_device_ptr(out)) {
+                CK(cudaMemcpyAsync(out, w->d_out, sizeof(double), cudaMemcpyDeviceToDevice, w->stream));
+            } else {
+                CK(cudaMemcpyAsync(w->h_out, w->d_out, sizeof(double), cudaMemcpyDeviceToHost, w->stream));
+                CK(cudaStreamSynchronize(w->stream));
+                *out = w->h_out[0];
+            }
+            return RBS_OK;
+        }
+    }
+    // the expansions could not hold every bit: the exact dot instead
+    if (fell_back) *fell_back = 1;
+    return rbs_exdot(x, y, n, out, stream);
+}

@@ -328,3 +328,74 @@ extern "C" int rbs_exdot_noalloc(int k, const double *const *xs, const double *c
     if (e != cudaSuccess) return set_error(RBS_ECUDA, "rbs_exdot_noalloc: kernel launch failed");
     return RBS_OK;
 }
+
+// ---- lightweight FPE-8 dot (Sec. 3.2) -----------------------------------------------
+//
+// The paper's lightweight variant: each thread keeps a floating-point
+// expansion of at most eight binary64 terms. A product enters as TwoProd's
+// r + s (Alg. 2) and each part is added with a cascade of TwoSums (Alg. 1)
+// that stops as soon as the carried error is zero (early exit). Where the
+// paper rounds the final expansion with NearSum, the terms here go into the
+// exact integer accumulator and are rounded once: the same correctly rounded
+// value. When a thread would need a ninth term, a TwoProd may be inexact
+// (|x*y| below 2^-969, where its error can underflow) or a value is not
+// finite, the kernel reports that information could be lost -- the paper's
+// warning -- and the entry point falls back to the exact dot.
+namespace rbs {
+
+__device__ __forceinline__ void fpe_two_sum(double a, double b, double &r, double &s) {
+    r = __dadd_rn(a, b);
+    const double z = __dsub_rn(r, a);
+    s = __dadd_rn(__dsub_rn(a, __dsub_rn(r, z)), __dsub_rn(b, z));
+}
+
+// c += x exactly while at most 8 terms are needed; false if a ninth is needed.
+__device__ __forceinline__ bool fpe_add(double (&c)[8], double x) {
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (x == 0.0) return true;
+        double r, s;
+        fpe_two_sum(c[k], x, r, s);
+        c[k] = r;
+        x = s;
+    }
+    return x == 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_fpe_dot(const double *__restrict__ x, const double *__restrict__ y,
+                                                 int64_t n, DotScratch *g, double *out, unsigned *lost) {
+    ExactR<1, 4> red;
+    red.init();
+    double c[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) c[k] = 0.0;
+    bool ok = true;
+    for (int64_t i = gtid(); i < n; i += gstride()) {
+        const double a = x[i], b = y[i];
+        const double r = __dmul_rn(a, b);
+        const double s = fma(a, b, -r);
+        const double ar = fabs(r);
+        if (!finite_d(r) || (ar < 0x1p-969 && (r != 0.0 || (a != 0.0 && b != 0.0)))) {
+            ok = false;
+            continue;
+        }
+        ok = fpe_add(c, r) && ok;
+        ok = fpe_add(c, s) && ok;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (!finite_d(c[k])) ok = false;
+        else red.add(0, c[k], 1.0);
+    }
+    if (!ok) atomicOr(lost, 1u);
+    __shared__ double vals[1];
+    if (red.finish(g, vals) && threadIdx.x == 0) *out = vals[0];
+}
+
+cudaError_t launch_fpe_dot(const double *x, const double *y, int64_t n, DotScratch *g, double *out,
+                           unsigned *lost, Cfg cfg, cudaStream_t s) {
+    k_fpe_dot<<<cfg.grid, cfg.block, 0, s>>>(x, y, n, g, out, lost);
+    return cudaGetLastError();
+}
+
+}  // namespace rbs

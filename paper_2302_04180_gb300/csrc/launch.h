@@ -34,6 +34,8 @@ cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys
                          DotScratch *g, double *out, int window, Cfg cfg, cudaStream_t s);
 cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, DotScratch *g,
                                  int64_t *limbs, int32_t *flags, int window, Cfg cfg, cudaStream_t s);
+cudaError_t launch_fpe_dot(const double *x, const double *y, int64_t n, DotScratch *g, double *out,
+                           unsigned *lost, Cfg cfg, cudaStream_t s);
 cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, cudaStream_t s);
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s);
