@@ -279,6 +279,7 @@ def run_gpu(args):
 
     kernels = _kernel_micro(rbs, gen, dev)
     batched = _batched(rbs, gen, dev)
+    serving = _serving(rbs, gen, dev)
     gpu_launches = sum(v[0] for v in prof_tot.values())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -287,7 +288,8 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
             "plain_comparator": {**plain, "repro_over_plain_time": plain["value"] / repro_one},
-            "pipelined": pipelined, "kernels": kernels, "batched": batched}
+            "pipelined": pipelined, "kernels": kernels, "batched": batched,
+            "serving": serving}
     if args.cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(A, b.cpu().numpy())
     print(json.dumps(line), flush=True)
@@ -333,6 +335,45 @@ def _batched(rbs, gen, dev):
             "total_iters": its, "converged": int(sum(r["converged"] for r in res))}
 
 
+def _serving(rbs, gen, dev, rates=(50.0, 150.0, 300.0), count=300, seed=3):
+    """Poisson-arrival solve requests against the continuous-batching server:
+    a pool of 48 systems (3D upwind convection-diffusion and 3D Poisson up to
+    128^3, classic/pipelined mix, tol 1e-8). Per rate: p50/p99 latency
+    (submission to completion), solves/s, and whether every answer is bitwise
+    the system's solo solve."""
+    import torch
+    pool = []
+    for A, v in gen.serving_pool(48, 0):
+        Ad = rbs.to_device(A, dev)
+        b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+        alone = rbs.rbs_solve(Ad, b, tol=1e-8, maxit=3000, variant=v, history=False)
+        pool.append((A, Ad, b, v, alone))
+    torch.cuda.synchronize()
+    out = []
+    for rate in rates:
+        arr = gen.poisson_arrivals(count, rate, seed)
+        picks = (gen.splitmix64(seed + 11, count) % np.uint64(len(pool))).astype(int)
+        with rbs.RbsServer() as srv:
+            tk = []
+            t0 = time.perf_counter()
+            for k in range(count):
+                while time.perf_counter() - t0 < arr[k]:
+                    time.sleep(0.0002)
+                A, Ad, b, v, _ = pool[picks[k]]
+                sd = {"A": Ad, "b": b, "x": torch.empty(A.n, dtype=torch.float64, device=dev),
+                      "tol": 1e-8, "maxit": 3000, "variant": v}
+                tk.append((srv.submit(sd), picks[k]))
+            res = [(srv.wait(t), p) for t, p in tk]
+            t1 = time.perf_counter()
+        lat = np.array([r["latency_s"] for r, _ in res])
+        same = all(r["iters"] == pool[p][4]["iters"] and torch.equal(r["x"], pool[p][4]["x"])
+                   for r, p in res)
+        out.append({"rate_per_s": rate, "requests": count, "solves_per_s": count / (t1 - t0),
+                    "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3), "identical_to_solo": bool(same)})
+    return out
+
+
 def _kernel_micro(rbs, gen, dev):
     """Standalone exact dot (2^27, cond 1e32) and SpMV (Poisson 128^3) GB/s."""
     import torch
@@ -368,6 +409,25 @@ def _kernel_micro(rbs, gen, dev):
     return out
 
 
+def run_serving(args):
+    """Serving sweep (10k requests per arrival rate) as its own JSON line."""
+    import torch
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2302_04180_gb300 as rbs
+    from paper_2302_04180_gb300 import gen
+    sweep = _serving(rbs, gen, dev, rates=(50.0, 100.0, 150.0, 200.0, 250.0), count=10000)
+    best = max(r["solves_per_s"] for r in sweep)
+    print(json.dumps({"metric": "serving solves/s at p99", "value": best, "unit": "solves/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "Poisson arrivals, 48-system pool (3D conv-diff, "
+                                             "3D Poisson up to 128^3), tol 1e-8"},
+                      "sweep": sweep}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,6 +440,8 @@ def main():
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="solver loop driver for untimed solves (timed solves use the host "
                          "driver, which records per-kernel CUDA events)")
+    ap.add_argument("--serving", action="store_true",
+                    help="only the serving sweep: 10k Poisson-arrival requests per rate")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip e2e, comparators and kernel microbenchmarks")
     args = ap.parse_args()
@@ -387,6 +449,8 @@ def main():
     GRID = args.grid
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
     return run_gpu(args)
 
 

@@ -253,6 +253,29 @@ typedef struct {
 int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
                       void *stream);
 
+/* ---- serving ---------------------------------------------------------------------
+ * A request loop with continuous batching (the library's own runtime; the
+ * paper has no counterpart). Clients submit solves at any time; `workers`
+ * threads, each with its own stream and workspace, take pending requests in
+ * arrival order while the Krylov state of the requests in flight stays within
+ * `budget_bytes` (one request always runs when none is in flight). A system
+ * with n >= solo_n runs alone with the whole-GPU solver (rbs_solve_ex); up to
+ * `max_batch` consecutive smaller ones run as one rbs_solve_batched launch (one
+ * thread-block cluster each). Requests arriving
+ * while others run are admitted as workers and budget free up; launches on
+ * different workers overlap on the device. Every answer is bitwise the one
+ * rbs_solve gives for that system alone. The caller keeps a submitted system's
+ * device buffers alive until its request is done. Latency = submission to
+ * completion; queue = submission to start. All handles and outputs are host. */
+typedef struct rbs_server rbs_server;
+int rbs_server_create(int32_t workers, int32_t max_batch, int64_t budget_bytes, int64_t solo_n,
+                      rbs_server **out);
+int rbs_server_submit(rbs_server *srv, const rbs_system *system, int64_t *ticket);
+int rbs_server_poll(rbs_server *srv, int64_t ticket, int32_t *done, rbs_info *info, double *latency_s,
+                    double *queue_s);
+int rbs_server_wait(rbs_server *srv, int64_t ticket, rbs_info *info, double *latency_s, double *queue_s);
+int rbs_server_destroy(rbs_server *srv);
+
 /* ---- library control ---------------------------------------------------------- */
 /* Synchronise `stream`, then return and clear the workspace error word:
  * RBS_OK, or RBS_EINVAL if a kernel met an out-of-range CSR index. */

@@ -35,7 +35,8 @@ PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv")
 # every symbol include/rbs.h declares
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
            "rbs_spmv_csr", "rbs_jacobi_invd", "rbs_jacobi_apply", "rbs_solve",
-           "rbs_solve_ex", "rbs_solve_batched", "rbs_fpe_dot", "rbs_stream_status", "rbs_release", "rbs_set_param",
+           "rbs_solve_ex", "rbs_solve_batched", "rbs_fpe_dot", "rbs_server_create",
+           "rbs_server_submit", "rbs_server_poll", "rbs_server_wait", "rbs_server_destroy", "rbs_stream_status", "rbs_release", "rbs_set_param",
            "rbs_get_param", "rbs_last_error", "rbs_version")
 
 
@@ -105,6 +106,11 @@ def load(path: str | None = None):
             "rbs_solve_ex": [C.POINTER(_Csr), vp, vp, vp, dbl, i32, i32, C.POINTER(_Opts), vp,
                              C.POINTER(_Info), C.POINTER(_Hist), C.POINTER(_Prof), vp],
             "rbs_fpe_dot": [vp, vp, i64, vp, vp, vp],
+            "rbs_server_create": [i32, i32, i64, i64, C.POINTER(vp)],
+            "rbs_server_submit": [vp, C.POINTER(_System), C.POINTER(i64)],
+            "rbs_server_poll": [vp, i64, C.POINTER(i32), C.POINTER(_Info), C.POINTER(dbl), C.POINTER(dbl)],
+            "rbs_server_wait": [vp, i64, C.POINTER(_Info), C.POINTER(dbl), C.POINTER(dbl)],
+            "rbs_server_destroy": [vp],
             "rbs_solve_batched": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist), vp],
             "rbs_stream_status": [vp],
             "rbs_release": [],
@@ -361,3 +367,51 @@ def rbs_solve_batched(systems, history=True, stream=None):
                     "tau_max": I.tau_max, "alpha0": I.alpha0, "mu0": I.mu0,
                     "hist": recs[i][: hists[i].len].copy() if history else None})
     return out
+
+
+class RbsServer:
+    """Continuous-batching solve server (see rbs_server_create in include/rbs.h).
+    submit(system_dict) -> ticket; wait(ticket) / poll(ticket) -> result dict with
+    latency_s and queue_s. Keep each system's tensors alive until it is done."""
+
+    def __init__(self, workers=8, max_batch=8, budget_bytes=16 << 30, solo_n=30000):
+        self._h = C.c_void_p()
+        _check(load().rbs_server_create(int(workers), int(max_batch), int(budget_bytes),
+                                        int(solo_n), C.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, sd) -> int:
+        sysc = _System(_csr(sd["A"]), _ptr(sd["b"]), _ptr(sd.get("x0")), _ptr(sd.get("jacobi_diag")),
+                       _ptr(sd["x"]), float(sd.get("tol", 1e-8)), int(sd.get("maxit", 1000)),
+                       int(sd.get("variant", RBS_CLASSIC)))
+        t = C.c_int64()
+        _check(load().rbs_server_submit(self._h, C.byref(sysc), C.byref(t)))
+        self._keep[t.value] = sd
+        return t.value
+
+    def _result(self, ticket, info, lat, que):
+        sd = self._keep.pop(ticket, None)
+        return {"x": sd["x"] if sd else None, "iters": info.iters, "converged": info.converged,
+                "status": info.status, "latency_s": lat.value, "queue_s": que.value}
+
+    def wait(self, ticket):
+        info, lat, que = _Info(), C.c_double(), C.c_double()
+        _check(load().rbs_server_wait(self._h, int(ticket), C.byref(info), C.byref(lat), C.byref(que)))
+        return self._result(ticket, info, lat, que)
+
+    def poll(self, ticket):
+        done, info, lat, que = C.c_int32(), _Info(), C.c_double(), C.c_double()
+        _check(load().rbs_server_poll(self._h, int(ticket), C.byref(done), C.byref(info),
+                                      C.byref(lat), C.byref(que)))
+        return self._result(ticket, info, lat, que) if done.value else None
+
+    def close(self):
+        if self._h:
+            load().rbs_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

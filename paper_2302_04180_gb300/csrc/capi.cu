@@ -312,6 +312,20 @@ int graph_loop(Workspace *w, const SolverArgs &a, int variant) {
 
 int set_error(int code, const char *msg) { return fail(code, msg); }
 
+void release_stream_workspace(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    Workspace *w = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ws.find(std::make_pair(dev, s));
+        if (it == g_ws.end()) return;
+        w = it->second;
+        g_ws.erase(it);
+    }
+    ws_free(w);
+}
+
 }  // namespace rbs
 
 using namespace rbs;

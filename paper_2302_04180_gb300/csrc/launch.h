@@ -28,6 +28,8 @@ struct Cfg {
 
 // Set the calling thread's rbs_last_error() message and return `code`.
 int set_error(int code, const char *msg);
+// Free the workspace of stream `s` on the current device (before the stream is destroyed).
+void release_stream_workspace(cudaStream_t s);
 
 // ---- standalone kernels (kernels_dot.cu) ----
 cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,

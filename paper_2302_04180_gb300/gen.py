@@ -364,3 +364,32 @@ def banded(n: int, band: int, perturb: float = 1e-4) -> CSR:
         vals_list.append(float(2 * band + 1) if off == 0 else (-(1.0 - perturb) if off < 0 else -1.0))
         masks.append(msk)
     return _stencil_csr(n, cols_list, vals_list, masks, f"banded_{n}_{band}")
+
+
+def serving_pool(count: int, seed: int, n_side_max: int = 128):
+    """Distinct systems that serving requests draw from: half 3D upwind
+    convection-diffusion (side log-uniform in [12, 64], Pe uniform in [0, 50],
+    random unit direction), half 3D Poisson (side log-uniform in [12,
+    n_side_max]); classic or pipelined with probability 1/2. Returns a list of
+    (CSR, variant) pairs."""
+    sid = lambda tag: stream_id(seed, 700 + tag)  # noqa: E731
+    u_kind, u_side, u_pe, u_var = (uniform(sid(t), count) for t in range(4))
+    dirs = uniform(sid(5), 3 * count).reshape(count, 3) * 2.0 - 1.0
+    out = []
+    for k in range(count):
+        if u_kind[k] < 0.5:
+            side = int(round(np.exp(np.log(12) + u_side[k] * (np.log(64) - np.log(12)))))
+            d = dirs[k] if np.any(dirs[k]) else np.ones(3)
+            A = convdiff3d(side, 50.0 * float(u_pe[k]), tuple(d))
+        else:
+            side = int(round(np.exp(np.log(12) + u_side[k] * (np.log(n_side_max) - np.log(12)))))
+            A = poisson3d(side)
+        out.append((A, 1 if u_var[k] >= 0.5 else 0))
+    return out
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process of the given rate."""
+    u = uniform(stream_id(seed, 800), count)
+    gaps = -np.log1p(-u) / rate
+    return np.cumsum(gaps)
