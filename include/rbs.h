@@ -28,10 +28,15 @@
  *  - Errors are returned as an int status (RBS_OK = 0); no C++ exception
  *    crosses the ABI. rbs_last_error() gives a one-line message for the
  *    calling thread's last failure.
- *  - Kernels never read out of bounds: every CSR index is checked on the
- *    device before use. A bad index is skipped and recorded in the
- *    workspace's error word; synchronising calls then return RBS_EINVAL, and
- *    asynchronous calls report it through rbs_stream_status().
+ *  - Kernels never read out of bounds. The standalone SpMV checks every CSR
+ *    index on the device before use; a bad index is kept in range and
+ *    recorded in the workspace's error word, and rbs_stream_status() (or a
+ *    synchronising call) then returns RBS_EINVAL. The solvers validate the
+ *    whole structure once at set-up (rowptr rising from 0 to nnz, columns in
+ *    [0, n)), return RBS_EINVAL if it fails, and then iterate with kernels
+ *    that do not re-check it: the matrix must not change during a solve.
+ *  - Device-side waits are bounded; one that expires (a staging copy that
+ *    never lands) returns RBS_ETIMEOUT instead of hanging.
  */
 #ifndef RBS_H
 #define RBS_H

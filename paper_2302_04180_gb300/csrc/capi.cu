@@ -64,9 +64,16 @@ struct Buf {
     size_t cap = 0;
 };
 
+// Graph capture (graph_loop) runs in whichever thread calls a solve, and the
+// serving runtime runs several such threads. cudaMalloc, cudaFree and device-
+// wide synchronisation in one thread must not overlap a capture in another,
+// so the library's own calls of that kind and its captures take this lock.
+std::mutex g_cap_mu;
+
 cudaError_t ensure(Buf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (b.cap >= bytes) return cudaSuccess;
+    std::lock_guard<std::mutex> cap(g_cap_mu);
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
@@ -114,6 +121,7 @@ int ws_get(cudaStream_t s, Workspace **out) {
         *out = it->second;
         return RBS_OK;
     }
+    std::lock_guard<std::mutex> cap(g_cap_mu);
     Workspace *w = new Workspace();
     w->dev = dev;
     w->stream = s;
@@ -137,6 +145,7 @@ int ws_get(cudaStream_t s, Workspace **out) {
 }
 
 void ws_free(Workspace *w) {
+    std::lock_guard<std::mutex> cap(g_cap_mu);
     cudaSetDevice(w->dev);
     if (w->stream) cudaStreamSynchronize(w->stream);
     else cudaDeviceSynchronize();
@@ -221,7 +230,8 @@ Cfg exdot_cfg(Workspace *w, int64_t n) {
 // Shared-memory carveout of the staging kernels. Measured on GB300 (Poisson
 // 256^3): 60-75 % of the unified L1/shared storage is best -- enough shared
 // memory for three 256-thread blocks per SM while L1 keeps the SpMV's x
-// gathers; the maximum split costs 25 %, a small one halves throughput.
+// gathers; the maximum split costs about 5 % (25 % with a third staging
+// buffer per warp), a small one halves throughput.
 int carveout_param() {
     const int64_t c = p_carveout.load();
     return (c >= 0 && c <= 100) ? (int)c : -1;
@@ -273,6 +283,7 @@ int graph_loop(Workspace *w, const SolverArgs &a, int variant) {
     std::string key((const char *)&a, sizeof a);
     key.append((const char *)&variant, sizeof variant);
     if (!(w->exec && key == w->graph_key)) {
+        std::lock_guard<std::mutex> cap(g_cap_mu);
         if (w->exec) cudaGraphExecDestroy(w->exec);
         if (w->graph) cudaGraphDestroy(w->graph);
         w->exec = nullptr;
@@ -366,6 +377,7 @@ int rbs_stream_status(void *stream) {
     unsigned err = 0;
     rc = read_err(w, &err);
     if (rc) return rc;
+    if (err & 4u) return fail(RBS_ETIMEOUT, "a bounded wait on an asynchronous copy expired");
     if (err) return fail(RBS_EINVAL, "a kernel met an out-of-range CSR index");
     return RBS_OK;
 }
@@ -474,9 +486,11 @@ int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream) {
     if ((rc = ws_get((cudaStream_t)stream, &w))) return rc;
     std::lock_guard<std::mutex> lk(w->mu);
     CSRArgs a{A->n, A->nnz, A->rowptr, A->col, A->val};
-    Cfg c = grid_for(w, A->n, block_of(p_spmv_block.load(), 256), 8);
+    const int sb = block_of(p_spmv_block.load(), 256);
+    const int carve = carveout_param();
+    Cfg c = grid_for(w, A->n, sb, spmv_blocks_per_sm(sb, carve));
     c.mode = p_spmv_mode.load() == 1 ? 1 : 0;
-    c.carveout = carveout_param();
+    c.carveout = carve;
     CK(launch_spmv(a, x, y, nullptr, &w->g->err, c, w->stream));
     return RBS_OK;
 }
@@ -584,11 +598,12 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
     a.dot_mode = o.dot_mode;
     {
         const int vb = block_of(p_vec_block.load(), 256);
-        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1);
+        const int carve = carveout_param();
+        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1, vb, carve);
         a.vec = grid_for(w, (n + 1) / 2, vb, bps);
         if (p_vec_grid.load() > 0) a.vec.grid = (int)p_vec_grid.load();
         const int sb = block_of(p_spmv_block.load(), 256);
-        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0));
+        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve));
         a.spmv.mode = p_spmv_mode.load() == 1 ? 1 : 0;
         a.carveout = carveout_param();
         a.spmv.carveout = a.carveout;
@@ -648,6 +663,7 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
     CK(cudaMemcpyAsync(h, w->st, sizeof *h, cudaMemcpyDeviceToHost, w->stream));
     CK(cudaStreamSynchronize(w->stream));
     if ((rc = read_err(w, &err))) return rc;
+    if (err & 4u) return fail(RBS_ETIMEOUT, "a bounded wait on an asynchronous copy expired");
     if (err) return fail(RBS_EINVAL, "a kernel met an out-of-range CSR index");
 
     info->iters = h->iter;

@@ -270,20 +270,21 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
 // contributions to limb base + j (at most 32 x 2^32 in magnitude), and one
 // conflict-free atomic per limb lands in the block accumulator. Windows spread
 // over more than 32 limbs fall back to per-lane atomics.
-constexpr int MAX_WARPS = 8;         // every kernel here runs blocks of at most 256 threads
-constexpr int WARP_SCRATCH = 6144;   // bytes of shared memory private to each warp
+constexpr int MAX_WARPS = 8;                        // every kernel here runs blocks of at most 256 threads
+constexpr int FLUSH_SCRATCH = 32 * 8 * 8 + 32 * 4;  // bytes of the warp_flush staging
 
-// Each warp's private slice of one shared buffer. Phases of a kernel that
-// stage data per warp (SpMV operands, then the window flush) reuse it; a warp
-// only ever touches its own slice, so no block barrier is needed between them.
-template <int BYTES = WARP_SCRATCH>
+// Each warp's private slice of one shared buffer of BYTES per warp. Phases of
+// a kernel that stage data per warp (SpMV operands, then the window flush)
+// reuse it by naming the same BYTES; a warp only ever touches its own slice,
+// so no block barrier is needed between them.
+template <int BYTES>
 __device__ __forceinline__ unsigned char *warp_scratch() {
+    static_assert(BYTES % 16 == 0, "16-byte aligned slices");
     __shared__ __align__(16) unsigned char buf[MAX_WARPS * BYTES];
     return buf + (threadIdx.x >> 5) * BYTES;
 }
-constexpr int FLUSH_SCRATCH = 32 * 8 * 8 + 32 * 4;  // staging of warp_flush
 
-template <int Q, int SCRATCH = WARP_SCRATCH>
+template <int Q, int SCRATCH = FLUSH_SCRATCH>
 __device__ __forceinline__ void warp_flush(Win<Q> &W, unsigned long long *sacc) {
     static_assert(SCRATCH >= FLUSH_SCRATCH, "flush staging");
     const unsigned FULL = 0xffffffffu;
@@ -405,14 +406,14 @@ static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t 
 // Grid-level finish of K exact reductions. Every thread of every block calls it
 // after its last exact_add. Returns true in the block that finishes last; there
 // the rounded values are in vals[0..K-1] (shared memory) after a barrier.
-template <int K, int Q>
+template <int K, int Q, int SCRATCH = FLUSH_SCRATCH>
 __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
                                              unsigned long long (*sacc)[NL], uint32_t *sflags,
                                              DotScratch *g, double *vals, bool export_limbs = false,
                                              long long *limbs_out = nullptr, int32_t *flags_out = nullptr) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        warp_flush<Q>(win[k], sacc[k]);
+        warp_flush<Q, SCRATCH>(win[k], sacc[k]);
         if (flags[k]) atomicOr(&sflags[k], flags[k]);
     }
     __syncthreads();

@@ -37,49 +37,153 @@ __device__ __forceinline__ double spmv_row(const CSRView &A, int64_t i, const do
     return acc;
 }
 
+// Error bits that kernels OR into the workspace error word.
+constexpr unsigned ERR_INDEX = 1u;    // an out-of-range CSR index or row pointer
+constexpr unsigned ERR_TIMEOUT = 4u;  // a bounded wait on an asynchronous copy expired
+
 // Warp-staged SpMV: each warp walks chunks of 32 consecutive rows. A chunk's
-// contiguous nonzero span (col, val) is copied into the warp's shared memory
-// with coalesced asynchronous copies, then every lane runs its own row: it
-// issues the x gathers of up to 8 entries at once, then the fma chain in stored
-// order. The walk is software-pipelined three chunks deep: the row pointers of
-// chunk c+2 are loading and the operands of chunk c+1 are copying (second
-// buffer) while chunk c computes. The arithmetic is exactly spmv_row's; only
-// the memory schedule differs. Spans longer than SPMV_CAP (or malformed row
-// pointers) take the per-lane path. fn(row, y_row) runs in the owning lane.
+// contiguous nonzero span (col, val), and the chunk's slice of an optional
+// companion vector z that the epilogue reads, are copied into the warp's shared
+// memory; then every lane runs its own row: it issues the x gathers of up to 8
+// entries at once, then the fma chain in stored order. The walk is software-
+// pipelined three chunks deep: the row pointers of chunk c+2 are loading and
+// the operands of chunk c+1 are copying (second buffer) while chunk c computes.
+// (A third buffer measured slower on GB300: the shared memory it takes comes
+// out of the L1 that serves the x gathers.)
+//
+// Copies: a full chunk whose arrays start on 16-byte boundaries is fetched by
+// one lane with three bulk asynchronous copies (the span rounded out to whole
+// 16-byte units, never past the end of the arrays) that complete on the
+// buffer's mbarrier; any other chunk by per-lane 16-byte (or, unaligned,
+// element) asynchronous copies. Spans longer than SPMV_CAP (or, when CHECKED,
+// malformed row pointers) take the per-lane unstaged path. With CHECKED every
+// index is range-checked and a bad one reported (ERR_INDEX); without it the
+// caller has validated the structure (rowptr monotone from 0 to nnz, columns
+// in [0, n)). The arithmetic is exactly spmv_row's; only the memory schedule
+// differs. fn(row, y_row, z_row) runs in the owning lane (z_row = 0 without z).
 // All 32 lanes of every warp must enter; blocks have at most MAX_WARPS warps.
-constexpr int SPMV_CAP = 256;
-constexpr int SPMV_BUF = SPMV_CAP * (sizeof(int32_t) + sizeof(double));  // 3 KB per buffer
+// Kernels that also flush exact windows name SPMV_SCRATCH so that the flush
+// reuses the same shared buffer.
+constexpr int SPMV_CAP = 224;                           // 32 rows of a 7-point stencil
+constexpr int SPMV_VAL_OFF = 32 * 8;                    // z slice first
+constexpr int SPMV_COL_OFF = SPMV_VAL_OFF + (SPMV_CAP + 2) * 8;
+constexpr int SPMV_BUF = SPMV_COL_OFF + (SPMV_CAP + 8) * 4;  // 2992 bytes per buffer
+constexpr int SPMV_SCRATCH = 2 * SPMV_BUF;                   // per warp: two buffers
+static_assert(SPMV_VAL_OFF % 16 == 0 && SPMV_COL_OFF % 16 == 0 && SPMV_BUF % 16 == 0, "16-byte units");
+static_assert(SPMV_SCRATCH >= FLUSH_SCRATCH, "the flush reuses the staging buffers");
+constexpr long long SPMV_WAIT_LIMIT = 1LL << 26;  // mbarrier polls before ERR_TIMEOUT
+
+enum : int { CHUNK_UNSTAGED = 0, CHUNK_LANES = 1, CHUNK_BULK = 2 };
 
 struct SpmvChunk {
     long long B;  // first nonzero of the chunk
-    int span;     // nonzeros in the chunk
-    bool staged;  // operands are in shared memory
+    int how;      // CHUNK_*
 };
 
+// First val / col element a staged chunk holds: the span rounded down to a
+// 16-byte unit for wide copies.
+__device__ __forceinline__ long long spmv_va(long long B, bool wide) { return wide ? (B & ~1LL) : B; }
+__device__ __forceinline__ long long spmv_ca(long long B, bool wide) { return wide ? (B & ~3LL) : B; }
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// One 16-byte asynchronous copy of which the first `src_bytes` are read from
+// global memory (the rest of the 16 shared bytes are zero-filled).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, unsigned src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+// mbarrier and bulk-copy primitives (one arrival per phase: the issuing lane's).
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Prepare chunk rb (row pointers b, e of this lane's row already loaded):
-// decide whether it can be staged and issue its copies into buffer `buf`.
-// Always commits one copy group, so group counting stays uniform.
-__device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t rb, long long b, long long e,
-                                                  unsigned char *buf) {
+// decide how it is staged and issue its copies into buffer `buf` (mbarrier
+// `bar` for bulk copies). Always commits one cp.async group, so group counting
+// stays uniform.
+template <bool CHECKED>
+__device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double *z, bool wide, bool bulk_ok,
+                                                  int64_t rb, long long b, long long e, unsigned char *buf,
+                                                  unsigned long long *bar) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    SpmvChunk c{0, 0, false};
+    SpmvChunk c{0, CHUNK_UNSTAGED};
     if (rb < A.n) {
         const bool live = rb + lane < A.n;
         const int last = (int)((A.n - 1 - rb) < 31 ? (A.n - 1 - rb) : 31);
         const long long B = __shfl_sync(FULL, b, 0);
         const long long E = __shfl_sync(FULL, e, last);
-        const bool ok = !live || (b >= B && e >= b && e <= E);
         const long long span = E - B;
         c.B = B;
-        c.span = (int)(span > 0 && span <= SPMV_CAP ? span : 0);
-        c.staged = __all_sync(FULL, ok) && B >= 0 && E <= A.nnz && span >= 0 && span <= SPMV_CAP;
-        if (c.staged) {
-            int32_t *scol = reinterpret_cast<int32_t *>(buf);
-            double *sval = reinterpret_cast<double *>(buf + SPMV_CAP * sizeof(int32_t));
-            for (int t = lane; t < c.span; t += 32) {
-                __pipeline_memcpy_async(scol + t, A.col + B + t, sizeof(int32_t));
-                __pipeline_memcpy_async(sval + t, A.val + B + t, sizeof(double));
+        bool ok = span >= 0 && span <= SPMV_CAP;
+        if (CHECKED) ok = __all_sync(FULL, !live || (b >= B && e >= b && e <= E)) && ok && B >= 0 && E <= A.nnz;
+        if (ok) {
+            double *sval = reinterpret_cast<double *>(buf + SPMV_VAL_OFF);
+            int32_t *scol = reinterpret_cast<int32_t *>(buf + SPMV_COL_OFF);
+            const long long va = spmv_va(B, wide), ca = spmv_ca(B, wide);
+            const long long ve = (E + 1) & ~1LL, ce = (E + 3) & ~3LL;
+            if (bulk_ok && last == 31 && ve <= A.nnz && ce <= A.nnz) {
+                c.how = CHUNK_BULK;
+                if (lane == 0) {
+                    const unsigned vbytes = (unsigned)(ve - va) * 8u, cbytes = (unsigned)(ce - ca) * 4u;
+                    const unsigned zbytes = z ? 256u : 0u;
+                    // earlier generic-proxy reads of this buffer happen before
+                    // the bulk copies overwrite it
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    mbar_arrive_expect_tx(bar, vbytes + cbytes + zbytes);
+                    if (vbytes) bulk_copy_g2s(sval, A.val + va, vbytes, bar);
+                    if (cbytes) bulk_copy_g2s(scol, A.col + ca, cbytes, bar);
+                    if (z) bulk_copy_g2s(buf, z + rb, 256u, bar);
+                }
+            } else {
+                c.how = CHUNK_LANES;
+                if (wide) {
+                    // 2 vals / 4 cols per unit; the last unit of an array reads
+                    // only the elements that exist
+                    const int nv = (int)((ve - va) >> 1), nc = (int)((ce - ca) >> 2);
+                    for (int u = lane; u < nv; u += 32) {
+                        const long long k = va + 2 * u;
+                        cp_async16(sval + 2 * u, A.val + k, A.nnz - k >= 2 ? 16u : 8u);
+                    }
+                    for (int u = lane; u < nc; u += 32) {
+                        const long long k = ca + 4 * u;
+                        const long long left = A.nnz - k;
+                        cp_async16(scol + 4 * u, A.col + k, left >= 4 ? 16u : (unsigned)left * 4u);
+                    }
+                } else {
+                    for (int t = lane; t < (int)span; t += 32) {
+                        __pipeline_memcpy_async(scol + t, A.col + B + t, sizeof(int32_t));
+                        __pipeline_memcpy_async(sval + t, A.val + B + t, sizeof(double));
+                    }
+                }
+                if (z && live)
+                    __pipeline_memcpy_async(reinterpret_cast<double *>(buf) + lane, z + rb + lane, 8);
             }
         }
     }
@@ -87,14 +191,27 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t rb, 
     return c;
 }
 
-template <class F>
-__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x, bool &bad,
-                                               F &&fn) {
-    static_assert(2 * SPMV_BUF <= WARP_SCRATCH, "warp scratch");
-    const int lane = threadIdx.x & 31;
+template <bool CHECKED, class F>
+__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x,
+                                               const double *__restrict__ z, unsigned &err, F &&fn) {
+    __shared__ __align__(8) unsigned long long s_bar[MAX_WARPS][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5) * 32;
-    int64_t rb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-    unsigned char *bufs = warp_scratch();
+    int64_t rb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * 32;
+    // valid columns are [0, ncol): with CHECKED the largest column of a row is
+    // tested once, and every gather stays in range
+    const unsigned ncol = A.n < 0x80000000LL ? (unsigned)A.n : 0x80000000u;
+    const bool wide = ((reinterpret_cast<uintptr_t>(A.col) | reinterpret_cast<uintptr_t>(A.val)) & 15) == 0;
+    const bool bulk_ok = wide && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
+    unsigned char *bufs = warp_scratch<SPMV_SCRATCH>();
+    unsigned long long *bars = s_bar[wid];
+    if (lane == 0) {
+        mbar_init(bars);
+        mbar_init(bars + 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncwarp();
+    unsigned parity = 0u;  // bit k: phase of buffer k's barrier to wait for
     auto rowptrs = [&](int64_t r0, long long &b, long long &e) {
         const int64_t r = r0 + lane;
         b = 0;
@@ -106,45 +223,69 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
     };
     long long b0, e0, b1, e1, b2, e2;
     rowptrs(rb, b0, e0);
-    SpmvChunk c0 = spmv_prepare(A, rb, b0, e0, bufs);
+    SpmvChunk c0 = spmv_prepare<CHECKED>(A, z, wide, bulk_ok, rb, b0, e0, bufs, bars);
     rowptrs(rb + step, b1, e1);
     int cur = 0;
     for (; rb < A.n; rb += step) {
-        const SpmvChunk c1 = spmv_prepare(A, rb + step, b1, e1, bufs + (cur ^ 1) * SPMV_BUF);
+        const SpmvChunk c1 =
+            spmv_prepare<CHECKED>(A, z, wide, bulk_ok, rb + step, b1, e1, bufs + (cur ^ 1) * SPMV_BUF, bars + (cur ^ 1));
         rowptrs(rb + 2 * step, b2, e2);
-        __pipeline_wait_prior(1);  // chunk rb's copies have landed
+        if (c0.how == CHUNK_BULK) {
+            long long spins = 0;
+            while (!mbar_try_wait(bars + cur, (parity >> cur) & 1u)) {
+                if (++spins > SPMV_WAIT_LIMIT) {
+                    err |= ERR_TIMEOUT;
+                    break;
+                }
+            }
+            parity ^= 1u << cur;
+        } else {
+            __pipeline_wait_prior(1);  // chunk rb's copies have landed
+        }
         __syncwarp();
         const int64_t r = rb + lane;
         if (r < A.n) {
-            double acc = 0.0;
-            if (c0.staged) {
-                const int32_t *scol = reinterpret_cast<const int32_t *>(bufs + cur * SPMV_BUF);
+            double acc = 0.0, zr = 0.0;
+            if (c0.how != CHUNK_UNSTAGED) {
+                const unsigned char *buf = bufs + cur * SPMV_BUF;
+                const int32_t *scol =
+                    reinterpret_cast<const int32_t *>(buf + SPMV_COL_OFF) + (b0 - spmv_ca(c0.B, wide));
                 const double *sval =
-                    reinterpret_cast<const double *>(bufs + cur * SPMV_BUF + SPMV_CAP * sizeof(int32_t));
-                const int lo = (int)(b0 - c0.B), hi = (int)(e0 - c0.B);
-                for (int k0 = lo; k0 < hi; k0 += 8) {
+                    reinterpret_cast<const double *>(buf + SPMV_VAL_OFF) + (b0 - spmv_va(c0.B, wide));
+                const int len = (int)(e0 - b0);
+                unsigned cmax = 0u;
+                for (int k0 = 0; k0 < len; k0 += 8) {
                     // all gathers first (up to 8 in flight), then the chain in
-                    // stored order; values and indices are re-read from shared
-                    // memory so only the gathered x stay in registers
+                    // stored order
                     double xv[8];
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
                         xv[j] = 0.0;
-                        if (k0 + j < hi) {
-                            const int32_t cidx = scol[k0 + j];
-                            if ((uint64_t)(int64_t)cidx < (uint64_t)A.n) xv[j] = __ldg(x + cidx);
-                            else bad = true;
+                        if (k0 + j < len) {
+                            const unsigned cidx = (unsigned)scol[k0 + j];
+                            if (CHECKED) {
+                                // a bad column is reported and its gather clamped
+                                // into range (the call fails; the value is moot)
+                                cmax = max(cmax, cidx);
+                                xv[j] = __ldg(x + min(cidx, ncol - 1u));
+                            } else {
+                                xv[j] = __ldg(x + cidx);
+                            }
                         }
                     }
 #pragma unroll
                     for (int j = 0; j < 8; j++)
-                        if (k0 + j < hi && (uint64_t)(int64_t)scol[k0 + j] < (uint64_t)A.n)
-                            acc = fma(sval[k0 + j], xv[j], acc);
+                        if (k0 + j < len) acc = fma(sval[k0 + j], xv[j], acc);
                 }
+                if (CHECKED && len > 0 && cmax >= ncol) err |= ERR_INDEX;
+                if (z) zr = reinterpret_cast<const double *>(buf)[lane];
             } else {
+                bool bad = false;
                 acc = spmv_row(A, r, x, bad);
+                if (bad) err |= ERR_INDEX;
+                if (z) zr = z[r];
             }
-            fn(r, acc);
+            fn(r, acc, zr);
         }
         __syncwarp();  // buffer `cur` is refilled two chunks later
         c0 = c1;
@@ -155,21 +296,26 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
         cur ^= 1;
     }
     __pipeline_wait_prior(0);
+    // a bulk chunk prepared past the end is never waited for: there is none,
+    // since prepare stages nothing for rb >= n
     __syncwarp();
 }
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
-// Row traversal of y = A x with epilogue fn(row, y_row): mode 0 warp-staged,
-// mode 1 one thread per row. Same bits either way.
-template <class F>
-__device__ __forceinline__ void spmv_each(const CSRView &A, const double *__restrict__ x, int mode, bool &bad,
-                                          F &&fn) {
+// Row traversal of y = A x with epilogue fn(row, y_row, z_row): mode 0
+// warp-staged, mode 1 one thread per row. Same bits either way. z may be null.
+// Error bits (ERR_*) accumulate in err.
+template <bool CHECKED, class F>
+__device__ __forceinline__ void spmv_each(const CSRView &A, const double *__restrict__ x,
+                                          const double *__restrict__ z, int mode, unsigned &err, F &&fn) {
     if (mode == 0) {
-        spmv_warp_rows(A, x, bad, fn);
+        spmv_warp_rows<CHECKED>(A, x, z, err, fn);
     } else {
-        for (int64_t i = gtid(); i < A.n; i += gstride()) fn(i, spmv_row(A, i, x, bad));
+        bool bad = false;
+        for (int64_t i = gtid(); i < A.n; i += gstride()) fn(i, spmv_row(A, i, x, bad), z ? z[i] : 0.0);
+        if (bad) err |= ERR_INDEX;
     }
 }
 

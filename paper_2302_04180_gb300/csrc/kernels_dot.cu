@@ -127,31 +127,54 @@ cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, doubl
     return cudaGetLastError();
 }
 
-// y = A x (Sec. 4.1), one thread per row, rows in a grid-stride loop. With a
-// solver state, the kernel is a no-op once the solver has stopped.
-__global__ void __launch_bounds__(256, 4) k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y,
+// y = A x (Sec. 4.1), warp-staged rows (mode 0) or one thread per row (mode
+// 1) in a grid-stride loop. CHECKED: every index is range-checked (the
+// standalone product); without it the solver has validated the structure at
+// set-up. With a solver state, the kernel is a no-op once the solver stopped.
+template <bool CHECKED>
+__global__ void __launch_bounds__(256, 3) k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y,
                                               const SolverState *st, unsigned *err, int mode) {
     if (st && st->done) return;
-    bool bad = false;
-    spmv_each(A, x, mode, bad, [&](int64_t i, double v) { y[i] = v; });
-    if (bad) atomicOr(err, 1u);
+    unsigned eb = 0u;
+    spmv_each<CHECKED>(A, x, nullptr, mode, eb, [&](int64_t i, double v, double) { y[i] = v; });
+    if (eb) atomicOr(err, eb);
 }
 
 static CSRView view(const CSRArgs &A) { return CSRView{A.n, A.nnz, A.rowptr, A.col, A.val}; }
 
+static void spmv_carveout(int c) {
+    static std::mutex mu;
+    static int applied[64];
+    static bool init = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!init) {
+        for (int i = 0; i < 64; i++) applied[i] = -2;
+        init = true;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && applied[dev] != c) {
+        cudaFuncSetAttribute(k_spmv<true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+        cudaFuncSetAttribute(k_spmv<false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+        cudaGetLastError();
+        applied[dev] = c;
+    }
+}
+
+int spmv_blocks_per_sm(int block, int carveout) {
+    spmv_carveout(carveout);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true>, block, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s) {
-    static int applied[64] = {-2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2,
-                              -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2,
-                              -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2,
-                              -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2, -2};
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && applied[dev] != cfg.carveout) {
-        cudaFuncSetAttribute(k_spmv, cudaFuncAttributePreferredSharedMemoryCarveout, cfg.carveout);
-        cudaGetLastError();
-        applied[dev] = cfg.carveout;
-    }
-    k_spmv<<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    spmv_carveout(cfg.carveout);
+    if (st) k_spmv<false><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    else k_spmv<true><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,10 @@
 //                                                -> tau, stop, beta, alpha (S16, S19)
 //   P4  t = A what                                                  (S18)
 // Once the stop flag is set, every later kernel returns at once.
+#include <mutex>
+
 #include "kernels.cuh"
+
 #include "launch.h"
 #include "tails.cuh"
 
@@ -70,18 +73,18 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
 
 // K1: s = A phat, <r0, s>
 template <class R>
-__global__ void __launch_bounds__(256, 4) k_cls_k1(Ctx c) {
+__global__ void __launch_bounds__(256, 3) k_cls_k1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
-    bool bad = false;
-    spmv_each(c.A, c.ph, c.spmv_mode, bad, [&](int64_t i, double si) {
+    unsigned eb = 0u;
+    spmv_each<false>(c.A, c.ph, c.r0, c.spmv_mode, eb, [&](int64_t i, double si, double r0) {
         c.s[i] = si;
-        red.add(0, c.r0[i], si);
+        red.add(0, r0, si);
     });
-    if (bad) atomicOr(c.err, 1u);
+    if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
+    if (red.template finish<SPMV_SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
 }
 
 // K2: q = fma(-alpha, s, r), qhat = q * invd
@@ -108,19 +111,19 @@ __global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
 
 // K3: y = A qhat, <q, y>, <y, y>
 template <class R>
-__global__ void __launch_bounds__(256, 4) k_cls_k3(Ctx c) {
+__global__ void __launch_bounds__(256, 3) k_cls_k3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
-    bool bad = false;
-    spmv_each(c.A, c.qh, c.spmv_mode, bad, [&](int64_t i, double yi) {
+    unsigned eb = 0u;
+    spmv_each<false>(c.A, c.qh, c.q, c.spmv_mode, eb, [&](int64_t i, double yi, double qi) {
         c.y[i] = yi;
-        red.add(0, c.q[i], yi);
+        red.add(0, qi, yi);
         red.add_sq(1, yi);
     });
-    if (bad) atomicOr(c.err, 1u);
+    if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
+    if (red.template finish<SPMV_SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
 }
 
 // K4: x = fma(omega, qhat, fma(alpha, phat, x)), r = fma(-omega, y, q), <r0,r>, <r,r>
@@ -206,17 +209,16 @@ template <class R>
 __global__ void __launch_bounds__(256) k_pipe_setup2(Ctx c) {
     R red;
     red.init();
-    bool bad = false;
-    spmv_each(c.A, c.rh, c.spmv_mode, bad, [&](int64_t i, double wi) {
+    unsigned eb = 0u;
+    spmv_each<false>(c.A, c.rh, c.r0, c.spmv_mode, eb, [&](int64_t i, double wi, double r0) {
         c.w[i] = wi;
         c.wh[i] = __dmul_rn(wi, c.invd[i]);
-        const double r0 = c.r0[i];
         red.add_sq(0, r0);  // r = r0 at set-up
         red.add(1, r0, wi);
     });
-    if (bad) atomicOr(c.err, 1u);
+    if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
+    if (red.template finish<SPMV_SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
 }
 
 // P1: S1-S4 (copies at iteration 0), S5-S7, S9; <q,y>, <y,y> -> omega
@@ -356,24 +358,30 @@ static void prefer_shared(int c) {
     cudaGetLastError();
 }
 
-cudaError_t solver_setup(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t) {
+// Apply the carveout to this device's kernels once per value. It must come
+// before any occupancy query, which depends on it.
+static void apply_carveout(int dot_mode, int c) {
+    static std::mutex mu;
     static int applied_exact[64], applied_plain[64];
     static bool init = false;
+    std::lock_guard<std::mutex> lk(mu);
     if (!init) {
         for (int i = 0; i < 64; i++) applied_exact[i] = applied_plain[i] = -2;
         init = true;
     }
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
-        const int c = a.carveout;
-        if (a.dot_mode == RBS_DOT_PLAIN && applied_plain[dev] != c) {
-            prefer_shared<PlainR<1>, PlainR<2>, PlainR<5>>(c);
-            applied_plain[dev] = c;
-        } else if (a.dot_mode != RBS_DOT_PLAIN && applied_exact[dev] != c) {
-            prefer_shared<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(c);
-            applied_exact[dev] = c;
-        }
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    if (dot_mode == RBS_DOT_PLAIN && applied_plain[dev] != c) {
+        prefer_shared<PlainR<1>, PlainR<2>, PlainR<5>>(c);
+        applied_plain[dev] = c;
+    } else if (dot_mode != RBS_DOT_PLAIN && applied_exact[dev] != c) {
+        prefer_shared<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(c);
+        applied_exact[dev] = c;
     }
+}
+
+cudaError_t solver_setup(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *t) {
+    apply_carveout(a.dot_mode, a.carveout);
     if (a.dot_mode == RBS_DOT_PLAIN) return setup_t<PlainR<1>, PlainR<2>, PlainR<5>>(a, variant, s, t);
     return setup_t<ExactR<1, SQ>, ExactR<2, SQ>, ExactR<5, SQ>>(a, variant, s, t);
 }
@@ -394,17 +402,31 @@ cudaError_t launch_set_cond(cudaGraphConditionalHandle h, SolverState *st, cudaS
     return cudaGetLastError();
 }
 
-int solver_blocks_per_sm(int variant, int dot_mode, int which) {
-    int nb = 0;
+int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout) {
+    apply_carveout(dot_mode, carveout);
+    if (which == 0 && variant == RBS_PIPELINED) return spmv_blocks_per_sm(block, carveout);
+    int nb = 0, nb2 = 0;
     cudaError_t e = cudaSuccess;
     if (dot_mode == RBS_DOT_PLAIN) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, 256, 0);
-    } else if (variant == RBS_PIPELINED) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, 256, 0);
+        if (which == 0) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<PlainR<1>>, block, 0);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<PlainR<2>>, block, 0);
+            nb = nb2 < nb ? nb2 : nb;
+        } else if (variant == RBS_PIPELINED) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, block, 0);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<PlainR<2>>, block, 0);
+        }
     } else if (which == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k3<ExactR<2, SQ>>, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<ExactR<1, SQ>>, block, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<ExactR<2, SQ>>, block, 0);
+        nb = nb2 < nb ? nb2 : nb;
+    } else if (variant == RBS_PIPELINED) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, block, 0);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<ExactR<2, SQ>>, 256, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<ExactR<2, SQ>>, block, 0);
     }
     if (e != cudaSuccess || nb < 1) nb = 1;
     return nb;

@@ -39,6 +39,9 @@ cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, Do
 cudaError_t launch_fpe_dot(const double *x, const double *y, int64_t n, DotScratch *g, double *out,
                            unsigned *lost, Cfg cfg, cudaStream_t s);
 cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, cudaStream_t s);
+// y = A x. Without a solver state every index is checked (ERR_INDEX on a bad
+// one); with one, the solver has validated the structure and the kernel skips
+// the checks (and does nothing once the solver has stopped).
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s);
 cudaError_t launch_jacobi_invd(const CSRArgs &A, const double *diag, double *invd, unsigned *err,
@@ -105,6 +108,9 @@ cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, int nsys
 int batch_max_clusters();
 
 // occupancy-derived persistent grid for the kernels of one kind
-int solver_blocks_per_sm(int variant, int dot_mode, int which);
+int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout);
+// Resident blocks per SM of the standalone SpMV kernel at this block size and
+// shared-memory carveout (applies the carveout first).
+int spmv_blocks_per_sm(int block, int carveout);
 
 }  // namespace rbs

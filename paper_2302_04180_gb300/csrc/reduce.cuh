@@ -37,9 +37,12 @@ struct ExactR {
     __device__ __forceinline__ void add_sq(int k, double x) {
         exact_add<Q, true>(win[k], flags[k], sacc[k], x, x);
     }
-    // true in the last block, with vals[0..K-1] rounded (shared memory)
+    // true in the last block, with vals[0..K-1] rounded (shared memory).
+    // SCRATCH: the per-warp scratch size the kernel already uses, so that the
+    // flush staging shares it.
+    template <int SCRATCH = FLUSH_SCRATCH>
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
-        return exact_finish<K, Q>(win, flags, sacc, sflags, g, vals);
+        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals);
     }
 };
 
@@ -69,13 +72,15 @@ struct ExactR2 {
     __device__ __forceinline__ void add(int k, double x, double y) {
         exact_add2<Q>(win[k], low[k], flags[k], sacc[k], x, y);
     }
+    template <int SCRATCH = FLUSH_SCRATCH>
     __device__ __forceinline__ void flush_low() {
 #pragma unroll
-        for (int k = 0; k < K; k++) warp_flush<Q>(low[k], sacc[k]);
+        for (int k = 0; k < K; k++) warp_flush<Q, SCRATCH>(low[k], sacc[k]);
     }
+    template <int SCRATCH = FLUSH_SCRATCH>
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
-        flush_low();
-        return exact_finish<K, Q>(win, flags, sacc, sflags, g, vals);
+        flush_low<SCRATCH>();
+        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals);
     }
 };
 
@@ -90,6 +95,7 @@ struct PlainR {
     }
     __device__ __forceinline__ void add(int k, double x, double y) { s[k] = fma(x, y, s[k]); }
     __device__ __forceinline__ void add_sq(int k, double x) { s[k] = fma(x, x, s[k]); }
+    template <int SCRATCH = 0>
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
         __shared__ double s_part[K][32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

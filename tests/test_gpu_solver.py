@@ -20,10 +20,11 @@ def dev():
 @pytest.fixture(scope="module")
 def rbs(dev):
     import paper_2302_04180_gb300 as m
+    carve = m.rbs_get_param("smem.carveout")
     yield m
     for k in ("vec.grid", "vec.block", "spmv.block", "spmv.mode", "solve.check_every"):
         m.rbs_set_param(k, 0)
-    m.rbs_set_param("smem.carveout", 75)
+    m.rbs_set_param("smem.carveout", carve)
 
 
 def _gpu_solve(rbs, dev, A, tol, maxit, variant, b=None, **kw):
@@ -87,6 +88,7 @@ def test_x0_and_given_diagonal(rbs, dev, orc, variant):
 def test_launch_shape_and_chunk_independence(rbs, dev, orc):
     A = gen.convdiff3d(14, 10.0)
     o = orc.solve(A, orc.spmv(A, np.ones(A.n)), tol=1e-10, maxit=500, variant=0)
+    carve = rbs.rbs_get_param("smem.carveout")
     for vg, vb, sb, ce, lm, sm, co in ((0, 0, 0, 0, 0, 0, 75), (0, 0, 0, 0, 1, 1, -1), (1, 32, 32, 1, 1, 0, 100),
                                        (7, 128, 64, 3, 0, 1, 50), (500, 256, 256, 50, 1, 0, 0),
                                        (152, 64, 128, 0, 0, 1, 75)):
@@ -102,7 +104,7 @@ def test_launch_shape_and_chunk_independence(rbs, dev, orc):
             _assert_same_run(g, ov)
     for k in ("vec.grid", "vec.block", "spmv.block", "spmv.mode"):
         rbs.rbs_set_param(k, 0)
-    rbs.rbs_set_param("smem.carveout", 75)
+    rbs.rbs_set_param("smem.carveout", carve)
 
 
 def test_run_to_run_bitwise(rbs, dev):
