@@ -428,6 +428,38 @@ def run_serving(args):
     return 0
 
 
+def run_micro_exdot(args):
+    """Standalone exact dots of seeded ill-conditioned vectors with known exact
+    results (the kernel microbenchmark's dot cases), one JSON line per case."""
+    import torch
+    import paper_2302_04180_gb300 as rbs
+    from paper_2302_04180_gb300 import gen
+    dev = torch.device("cuda:0")
+    for case in args.micro_exdot.split(","):
+        lg, cond = case.split(":")
+        n = 1 << int(lg)
+        x, y, exact = gen.ill_conditioned_dot(n, float(cond), 0)
+        xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+        del x, y
+        o = torch.empty(1, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            rbs.rbs_exdot(xt, yt, o)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            rbs.rbs_exdot(xt, yt, o)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / max(args.steps, 1)
+        print(json.dumps({"kernel": "exdot", "n": n, "cond": float(cond), "us": ms * 1e3,
+                          "GB/s": 16 * n / (ms * 1e-3) / 1e9,
+                          "matches_exact": None if exact is None else bool(float(o.cpu()) == float(exact))}),
+              flush=True)
+        del xt, yt
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,6 +476,9 @@ def main():
                     help="only the serving sweep: 10k Poisson-arrival requests per rate")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip e2e, comparators and kernel microbenchmarks")
+    ap.add_argument("--micro-exdot", default=None, metavar="LOG2N:COND[,...]",
+                    help="only the standalone exact-dot microbenchmark on these cases "
+                         "(e.g. 24:1e32 or 20:1,27:1e48); the profiling target of the exdot")
     args = ap.parse_args()
     global GRID
     GRID = args.grid
@@ -451,6 +486,8 @@ def main():
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.micro_exdot:
+        return run_micro_exdot(args)
     return run_gpu(args)
 
 

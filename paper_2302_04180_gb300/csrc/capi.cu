@@ -209,15 +209,16 @@ Cfg grid_for(Workspace *w, int64_t items, int block, int per_sm) {
     return c;
 }
 
-// Exact-dot launch shape: persistent grid, and never more than 2^20 products
-// per thread per launch (the register window's headroom).
-Cfg exdot_cfg(Workspace *w, int64_t n) {
+// Exact-dot launch shape: a persistent grid of whole waves (blocks_per_sm
+// resident blocks on every SM), and never more than 2^20 products per thread
+// per launch (the register window's headroom).
+Cfg persistent_cfg(Workspace *w, int64_t n, int blocks_per_sm, int block) {
     Cfg c;
-    c.block = block_of(p_exdot_block.load(), 256);
+    c.block = block;
     int64_t g = p_exdot_grid.load();
     if (g <= 0) {
         int64_t need = (n + 2LL * c.block - 1) / (2LL * c.block);
-        int64_t cap = (int64_t)w->sms * 4;
+        int64_t cap = (int64_t)w->sms * blocks_per_sm;
         g = need < 1 ? 1 : (need < cap ? need : cap);
     }
     int64_t minimum = (n + ((int64_t)c.block << 20) - 1) / ((int64_t)c.block << 20);
@@ -225,6 +226,10 @@ Cfg exdot_cfg(Workspace *w, int64_t n) {
     if (g > 0x7fffffff) g = 0x7fffffff;
     c.grid = (int)g;
     return c;
+}
+Cfg exdot_cfg(Workspace *w, int64_t n, int k, int window) {
+    const int block = block_of(p_exdot_block.load(), 256);
+    return persistent_cfg(w, n, exdot_blocks_per_sm(k, window, block), block);
 }
 
 // Shared-memory carveout of the staging kernels. Measured on GB300 (Poisson
@@ -411,7 +416,7 @@ static int exdot_common(int k, const double *const *xs, const double *const *ys,
         if ((rc = to_device(w, (2 * j + 1) % 8, ys[j], (size_t)n * 8, &p))) return rc;
         dy[j] = (const double *)p;
     }
-    CK(launch_exdot(k, dx, dy, n, w->g, dout, window_param(), exdot_cfg(w, n), w->stream));
+    CK(launch_exdot(k, dx, dy, n, w->g, dout, window_param(), exdot_cfg(w, n, k, window_param()), w->stream));
     if (!out_dev) {
         CK(cudaMemcpyAsync(w->h_out, w->d_out, k * sizeof(double), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaStreamSynchronize(w->stream));
@@ -448,7 +453,7 @@ int rbs_exdot_partial(const double *x, const double *y, int64_t n, int64_t *limb
         CK(cudaMemsetAsync(flags, 0, sizeof(int32_t), w->stream));
         return RBS_OK;
     }
-    CK(launch_exdot_partial(x, y, n, w->g, limbs, flags, 4, exdot_cfg(w, n), w->stream));
+    CK(launch_exdot_partial(x, y, n, w->g, limbs, flags, 4, exdot_cfg(w, n, 1, 4), w->stream));
     return RBS_OK;
 }
 
@@ -836,7 +841,8 @@ extern "C" int rbs_fpe_dot(const double *x, const double *y, int64_t n, double *
         if ((rc = to_device(w, 0, x, (size_t)n * 8, &dx))) return rc;
         if ((rc = to_device(w, 1, y, (size_t)n * 8, &dy))) return rc;
         CK(cudaMemsetAsync(&w->g->err, 0, sizeof(unsigned), w->stream));
-        Cfg c = exdot_cfg(w, n);
+        const int fb = block_of(p_exdot_block.load(), 256);
+        Cfg c = persistent_cfg(w, n, fpe_blocks_per_sm(fb), fb);
         CK(launch_fpe_dot((const double *)dx, (const double *)dy, n, w->g, w->d_out, &w->g->err, c, w->stream));
         unsigned lost = 0;
         if ((rc = read_err(w, &lost))) return rc;

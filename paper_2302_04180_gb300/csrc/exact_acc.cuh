@@ -213,15 +213,25 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
                                            double x, double y) {
     const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
     const uint32_t yh = (uint32_t)__double2hiint(y), yl = (uint32_t)__double2loint(y);
-    const uint32_t ex = (xh >> 20) & 0x7ffu, ey = (yh >> 20) & 0x7ffu;
-    if (ex == 0x7ffu || ey == 0x7ffu) {
-        flags |= special_flags(xh, xl, yh, yl);
-        return;
+    const uint32_t exm = xh & 0x7ff00000u, eym = yh & 0x7ff00000u;  // biased exponents << 20
+    uint32_t A1, B1;
+    int pos;
+    if (exm - 0x00100000u < 0x7fe00000u && eym - 0x00100000u < 0x7fe00000u) {
+        // both operands normal (the common case): implicit bit set, no zero
+        A1 = (xh & 0xfffffu) | 0x100000u;
+        B1 = (yh & 0xfffffu) | 0x100000u;
+        pos = (int)((exm >> 20) + (eym >> 20)) - 2;
+    } else {
+        const uint32_t ex = exm >> 20, ey = eym >> 20;
+        if (ex == 0x7ffu || ey == 0x7ffu) {
+            flags |= special_flags(xh, xl, yh, yl);
+            return;
+        }
+        A1 = (xh & 0xfffffu) | (ex ? 0x100000u : 0u);
+        B1 = (yh & 0xfffffu) | (ey ? 0x100000u : 0u);
+        if ((A1 | xl) == 0u || (B1 | yl) == 0u) return;
+        pos = (int)max(ex, 1u) + (int)max(ey, 1u) - 2;
     }
-    const uint32_t A1 = (xh & 0xfffffu) | (ex ? 0x100000u : 0u);
-    const uint32_t B1 = (yh & 0xfffffu) | (ey ? 0x100000u : 0u);
-    if ((A1 | xl) == 0u || (B1 | yl) == 0u) return;
-    const int pos = (int)max(ex, 1u) + (int)max(ey, 1u) - 2;
     const unsigned long long m00 = (unsigned long long)xl * yl;
     const unsigned long long m01 = (unsigned long long)xl * B1 + (m00 >> 32);
     const unsigned long long m10 = (unsigned long long)A1 * yl + (uint32_t)m01;

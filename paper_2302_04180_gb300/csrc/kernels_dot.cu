@@ -96,6 +96,32 @@ static cudaError_t exdot_q(int k, const double *const *xs, const double *const *
     }
 }
 
+template <int Q>
+static int exdot_occ_q(int k, int block) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (k) {
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<1, Q, false>, block, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<2, Q, false>, block, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<3, Q, false>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<4, Q, false>, block, 0); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<5, Q, false>, block, 0); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<6, Q, false>, block, 0); break;
+        default: break;
+    }
+    if (e != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
+int exdot_blocks_per_sm(int k, int window, int block) {
+    if (window == 2) return exdot_occ_q<2>(k, block);
+    if (window == 1) return exdot_occ_q<1>(k, block);
+    return exdot_occ_q<4>(k, block);
+}
+
 cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,
                          DotScratch *g, double *out, int window, Cfg cfg, cudaStream_t s) {
     if (window == 2) return exdot_q<2>(k, xs, ys, n, g, out, cfg, s);
@@ -413,6 +439,15 @@ __global__ void __launch_bounds__(256) k_fpe_dot(const double *__restrict__ x, c
     if (!ok) atomicOr(lost, 1u);
     __shared__ double vals[1];
     if (red.finish(g, vals) && threadIdx.x == 0) *out = vals[0];
+}
+
+int fpe_blocks_per_sm(int block) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fpe_dot, block, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
 }
 
 cudaError_t launch_fpe_dot(const double *x, const double *y, int64_t n, DotScratch *g, double *out,
