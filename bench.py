@@ -314,7 +314,9 @@ def _traffic():
 
 def _batched(rbs, gen, dev):
     """512 independent convection-diffusion systems (2D/3D, n 1k-300k, Pe 0-50,
-    classic/pipelined mix, tol 1e-8) in one persistent cluster launch."""
+    classic/pipelined mix, tol 1e-8) in one persistent cluster launch: timed
+    under the default schedule, then autotuned (proxy solves weighted by the
+    first solve's iteration counts) and timed under the tuned schedule."""
     import torch
     work = gen.batch_workload(512, seed=0)
     systems = []
@@ -323,16 +325,30 @@ def _batched(rbs, gen, dev):
         b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
         systems.append({"A": Ad, "b": b, "x": torch.empty(A.n, dtype=torch.float64, device=dev),
                         "tol": 1e-8, "maxit": 5000, "variant": v})
-    rbs.rbs_solve_batched(systems, history=False)
-    torch.cuda.synchronize()
+    default = {"cluster": 8, "split": 0}
+
+    def timed(schedule):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        res = rbs.rbs_solve_batched(systems, history=False, schedule=schedule)
+        torch.cuda.synchronize()
+        return res, time.perf_counter() - t
+
+    first = rbs.rbs_solve_batched(systems, history=False, schedule=default)
+    res0, dt0 = timed(default)
+    x0s = [r["x"].clone() for r in res0]
     t = time.perf_counter()
-    res = rbs.rbs_solve_batched(systems, history=False)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t
+    best = rbs.rbs_batch_tune(systems, prev=first, proxy_iters=24)
+    tune_s = time.perf_counter() - t
+    res, dt = timed({"cluster": best["cluster"], "split": best["split"]})
+    same = all(a["iters"] == b["iters"] and bool(torch.equal(a["x"], x)) for a, b, x in zip(res, res0, x0s))
     its = sum(r["iters"] for r in res)
     return {"systems": len(systems), "unknowns": int(sum(A.n for A, _ in work)),
             "seconds": dt, "systems_per_s": len(systems) / dt, "iters_per_s": its / dt,
-            "total_iters": its, "converged": int(sum(r["converged"] for r in res))}
+            "total_iters": its, "converged": int(sum(r["converged"] for r in res)),
+            "schedule": {"cluster": best["cluster"], "split": best["split"]},
+            "tuning_seconds": tune_s, "default_schedule": default, "default_seconds": dt0,
+            "identical_to_default": same}
 
 
 def _serving(rbs, gen, dev, rates=(50.0, 150.0, 300.0), count=300, seed=3):
@@ -428,6 +444,42 @@ def run_serving(args):
     return 0
 
 
+def run_solve_only(args):
+    """Warm-up and timed solves of one variant on the Poisson --grid workload
+    (host loop, per-kernel CUDA events), one JSON line: a profiling target."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import paper_2302_04180_gb300 as rbs
+    from paper_2302_04180_gb300 import gen
+    dev = torch.device("cuda:0")
+    A = gen.poisson3d(GRID)
+    Ad = rbs.to_device(A, dev)
+    b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    variant = 1 if args.solve_only == "pipelined" else 0
+    for _ in range(args.warmup):
+        rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=variant, x_out=x, loop_mode=1)
+    tot, iters = {}, 0
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        r = rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=variant, x_out=x, profile=True,
+                          loop_mode=1)
+        iters += r["iters"]
+        for k, (nl, ms) in r["prof"].items():
+            a = tot.setdefault(k, [0, 0.0])
+            a[0] += nl
+            a[1] += ms
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    print(json.dumps({"variant": args.solve_only, "grid": GRID, "iters": iters,
+                      "iters_per_s": iters / dt,
+                      "us_per_launch": {k: v[1] * 1e3 / max(v[0], 1) for k, v in tot.items() if v[0]},
+                      "launches": {k: v[0] for k, v in tot.items() if v[0]}}), flush=True)
+    return 0
+
+
 def run_micro_exdot(args):
     """Standalone exact dots of seeded ill-conditioned vectors with known exact
     results (the kernel microbenchmark's dot cases), one JSON line per case."""
@@ -476,6 +528,9 @@ def main():
                     help="only the serving sweep: 10k Poisson-arrival requests per rate")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip e2e, comparators and kernel microbenchmarks")
+    ap.add_argument("--solve-only", default=None, choices=["classic", "pipelined"],
+                    help="only warm-up + timed solves of this variant on the --grid workload, "
+                         "with per-kernel CUDA-event times (a profiling target)")
     ap.add_argument("--micro-exdot", default=None, metavar="LOG2N:COND[,...]",
                     help="only the standalone exact-dot microbenchmark on these cases "
                          "(e.g. 24:1e32 or 20:1,27:1e48); the profiling target of the exdot")
@@ -488,6 +543,8 @@ def main():
         return run_serving(args)
     if args.micro_exdot:
         return run_micro_exdot(args)
+    if args.solve_only:
+        return run_solve_only(args)
     return run_gpu(args)
 
 

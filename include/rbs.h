@@ -258,6 +258,41 @@ typedef struct {
 int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
                       void *stream);
 
+/* Schedule of a batched launch (the library's own tuning; the paper has
+ * none). The launch is made of thread-block clusters of `cluster` CTAs (1, 2,
+ * 4, 8 or 16; 16 needs the device's non-portable cluster size). Systems are
+ * queued largest first; one with at least `split` unknowns is solved by a
+ * whole cluster (rows split across its CTAs, dots reduced through distributed
+ * shared memory), and from the first smaller one on every CTA takes systems
+ * alone. `ms` is the tuner's measured time of its proxy run (0 otherwise).
+ * Results never depend on the schedule: every system's iterates are bitwise
+ * those of rbs_solve. */
+typedef struct {
+    int32_t cluster;
+    int32_t pad;
+    int64_t split;
+    double ms;
+} rbs_batch_schedule;
+
+/* rbs_solve_batched with an explicit schedule (NULL: the schedule the last
+ * rbs_batch_tune on this device chose, else cluster 8 and split 0). Returns
+ * RBS_EINVAL for a malformed schedule or one whose clusters do not fit. */
+int rbs_solve_batched_ex(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                         const rbs_batch_schedule *sched, void *stream);
+
+/* Autotune the batched schedule for this batch: times proxy solves of the
+ * systems (each stopped after a number of iterations) under candidate
+ * schedules -- every cluster size at the median split, then every split
+ * candidate (system-size quantiles, 0 and "no cluster") at the best size --
+ * and returns the fastest in *best, which later rbs_solve_batched calls on this
+ * device use. The proxy iteration cap of system i is proxy_iters, or, given a
+ * previous solve's infos (`prev`, nsys entries, nullable), proxy_iters scaled
+ * by prev[i].iters / max_j prev[j].iters so that systems keep their relative
+ * costs. Proxy solves write x into library scratch, not the callers' buffers,
+ * and keep no history. Synchronises the stream. */
+int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs_info *prev, int32_t proxy_iters,
+                   rbs_batch_schedule *best, void *stream);
+
 /* ---- serving ---------------------------------------------------------------------
  * A request loop with continuous batching (the library's own runtime; the
  * paper has no counterpart). Clients submit solves at any time; `workers`

@@ -35,7 +35,8 @@ PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv")
 # every symbol include/rbs.h declares
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
            "rbs_spmv_csr", "rbs_jacobi_invd", "rbs_jacobi_apply", "rbs_solve",
-           "rbs_solve_ex", "rbs_solve_batched", "rbs_fpe_dot", "rbs_server_create",
+           "rbs_solve_ex", "rbs_solve_batched", "rbs_solve_batched_ex", "rbs_batch_tune", "rbs_fpe_dot",
+           "rbs_server_create",
            "rbs_server_submit", "rbs_server_poll", "rbs_server_wait", "rbs_server_destroy", "rbs_stream_status", "rbs_release", "rbs_set_param",
            "rbs_get_param", "rbs_last_error", "rbs_version")
 
@@ -112,6 +113,10 @@ def load(path: str | None = None):
             "rbs_server_wait": [vp, i64, C.POINTER(_Info), C.POINTER(dbl), C.POINTER(dbl)],
             "rbs_server_destroy": [vp],
             "rbs_solve_batched": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist), vp],
+            "rbs_solve_batched_ex": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist),
+                                     C.POINTER(_Schedule), vp],
+            "rbs_batch_tune": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.c_int32,
+                               C.POINTER(_Schedule), vp],
             "rbs_stream_status": [vp],
             "rbs_release": [],
             "rbs_set_param": [C.c_char_p, i64],
@@ -335,29 +340,47 @@ def rbs_solve(A, b, x0=None, jacobi_diag=None, tol=1e-8, maxit=1000, variant=RBS
     }
 
 
-def rbs_solve_batched(systems, history=True, stream=None):
-    """Solve many independent systems in one persistent launch. `systems` is a
-    list of dicts with keys A (DeviceCSR), b, x (device tensors), and optional
-    x0, jacobi_diag, tol (1e-8), maxit (1000), variant (0). Returns a list of
-    per-system dicts like rbs_solve's (x is the caller's tensor)."""
+class _Schedule(C.Structure):
+    _fields_ = [("cluster", C.c_int32), ("pad", C.c_int32), ("split", C.c_int64), ("ms", C.c_double)]
+
+
+def _systems(systems, history):
     nsys = len(systems)
     arr = (_System * nsys)()
-    infos = (_Info * nsys)()
     hists = (_Hist * nsys)()
     recs = []
     for i, sd in enumerate(systems):
         A = sd["A"]
         arr[i] = _System(_csr(A), _ptr(sd["b"]), _ptr(sd.get("x0")), _ptr(sd.get("jacobi_diag")),
-                         _ptr(sd["x"]), float(sd.get("tol", 1e-8)), int(sd.get("maxit", 1000)),
+                         _ptr(sd.get("x")), float(sd.get("tol", 1e-8)), int(sd.get("maxit", 1000)),
                          int(sd.get("variant", RBS_CLASSIC)))
         cap = max(int(sd.get("maxit", 1000)), 1) if history else 0
         rec = np.empty((max(cap, 1), RBS_HIST_W), dtype=np.float64)
         recs.append(rec)
         hists[i] = _Hist(cap, 0, rec.ctypes.data)
+    return arr, hists, recs
+
+
+def rbs_solve_batched(systems, history=True, stream=None, schedule=None):
+    """Solve many independent systems in one persistent launch. `systems` is a
+    list of dicts with keys A (DeviceCSR), b, x (device tensors), and optional
+    x0, jacobi_diag, tol (1e-8), maxit (1000), variant (0). `schedule`: a dict
+    {"cluster", "split"} (see rbs_batch_schedule), None for the tuned or default
+    one. Returns a list of per-system dicts like rbs_solve's (x is the caller's
+    tensor)."""
+    nsys = len(systems)
+    arr, hists, recs = _systems(systems, history)
+    infos = (_Info * nsys)()
     first = systems[0]["b"] if nsys else None
-    rc = load().rbs_solve_batched(nsys, arr, infos, hists if history else None,
-                                  _stream(stream, first))
-    if rc not in (RBS_OK, RBS_EINVAL):
+    sch = None
+    if schedule is not None:
+        sch = _Schedule(int(schedule["cluster"]), 0, int(schedule.get("split", 0)), 0.0)
+    rc = load().rbs_solve_batched_ex(nsys, arr, infos, hists if history else None,
+                                     C.byref(sch) if sch is not None else None, _stream(stream, first))
+    # RBS_EINVAL with per-system statuses marks invalid systems (the others are
+    # solved); without any, the call itself was rejected (e.g. its schedule)
+    if rc not in (RBS_OK, RBS_EINVAL) or (rc == RBS_EINVAL and
+                                          not any(infos[i].status == RBS_EINVAL for i in range(nsys))):
         _check(rc)
     out = []
     for i in range(nsys):
@@ -367,6 +390,24 @@ def rbs_solve_batched(systems, history=True, stream=None):
                     "tau_max": I.tau_max, "alpha0": I.alpha0, "mu0": I.mu0,
                     "hist": recs[i][: hists[i].len].copy() if history else None})
     return out
+
+
+def rbs_batch_tune(systems, prev=None, proxy_iters=24, stream=None):
+    """Autotune the batched schedule (see rbs_batch_tune in include/rbs.h).
+    prev: the result list of an earlier rbs_solve_batched of the same systems
+    (its iteration counts weight the proxy solves). Returns {"cluster",
+    "split", "ms"}; later rbs_solve_batched calls on this device use it."""
+    nsys = len(systems)
+    arr, _, _ = _systems(systems, False)
+    pinfo = None
+    if prev is not None:
+        pinfo = (_Info * nsys)()
+        for i, r in enumerate(prev):
+            pinfo[i].iters = int(r["iters"])
+    best = _Schedule()
+    first = systems[0]["b"] if nsys else None
+    _check(load().rbs_batch_tune(nsys, arr, pinfo, int(proxy_iters), C.byref(best), _stream(stream, first)))
+    return {"cluster": best.cluster, "split": best.split, "ms": best.ms}
 
 
 class RbsServer:

@@ -709,38 +709,56 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
 
 }  // extern "C"
 
-extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
-                                 void *stream) {
-    if (nsys < 0 || (nsys > 0 && (!systems || !infos))) return fail(RBS_EINVAL, "bad batch arguments");
-    if (nsys == 0) return RBS_OK;
-    Workspace *w;
-    int rc = ws_get((cudaStream_t)stream, &w);
-    if (rc) return rc;
-    std::lock_guard<std::mutex> lk(w->mu);
+// ---- batched solves and their schedule tuner ---------------------------------
+
+namespace {
+
+std::mutex g_tuned_mu;
+std::map<int, rbs_batch_schedule> g_tuned;  // per device: the last tuned schedule
+
+rbs_batch_schedule default_schedule() {
+    rbs_batch_schedule d;
+    memset(&d, 0, sizeof d);
+    d.cluster = 8;
+    d.split = 0;  // every system solved by a whole cluster
+    return d;
+}
+
+bool schedule_ok(const rbs_batch_schedule &s) {
+    return s.cluster >= 1 && s.cluster <= 16 && (s.cluster & (s.cluster - 1)) == 0 && s.split >= 0;
+}
+
+// Solve the batch with schedule `sched`. With proxy_maxit (nsys entries) each
+// system stops after that many iterations and writes x into library scratch
+// instead of the caller's buffer (the tuner's timing runs); *ms gets the
+// device time of the prepare + solve launches.
+int batch_solve(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                const rbs_batch_schedule &sched, const int32_t *proxy_maxit, float *ms) {
     std::vector<BatchSys> sys((size_t)nsys);
     std::vector<char> valid((size_t)nsys, 1);
     size_t work_elems = 0, hist_recs = 0;
+    const bool proxy = proxy_maxit != nullptr;
     for (int i = 0; i < nsys; i++) {
         const rbs_system &S = systems[i];
         memset(&infos[i], 0, sizeof infos[i]);
         bool ok = S.A.n > 0 && S.A.n <= 0x7fffffff && S.A.nnz >= 0 && S.A.rowptr &&
-                  (S.A.nnz == 0 || (S.A.col && S.A.val)) && S.b && S.x && S.maxit >= 0 && S.tol >= 0.0 &&
-                  (S.variant == RBS_CLASSIC || S.variant == RBS_PIPELINED);
-        ok = ok && is_device_ptr(S.A.rowptr) && is_device_ptr(S.b) && is_device_ptr(S.x) &&
+                  (S.A.nnz == 0 || (S.A.col && S.A.val)) && S.b && (S.x || proxy) && S.maxit >= 0 &&
+                  S.tol >= 0.0 && (S.variant == RBS_CLASSIC || S.variant == RBS_PIPELINED);
+        ok = ok && is_device_ptr(S.A.rowptr) && is_device_ptr(S.b) && (proxy || is_device_ptr(S.x)) &&
              (S.A.nnz == 0 || (is_device_ptr(S.A.col) && is_device_ptr(S.A.val))) &&
              (!S.x0 || is_device_ptr(S.x0)) && (!S.jacobi_diag || is_device_ptr(S.jacobi_diag));
         if (hists && (hists[i].cap < 0 || (hists[i].cap > 0 && !hists[i].rec))) ok = false;
         valid[(size_t)i] = ok;
         if (!ok) continue;
         const int64_t stride = (S.A.n + 31) / 32 * 32;
-        work_elems += (size_t)stride * (S.variant == RBS_PIPELINED ? 17 : 9);
+        work_elems += (size_t)stride * ((S.variant == RBS_PIPELINED ? 17 : 9) + (proxy ? 1 : 0));
         const int cap = hists ? std::min(hists[i].cap, S.maxit) : 0;
         hist_recs += (size_t)(cap > 0 ? cap : 0);
     }
     CK(ensure(w->batch_work, work_elems * 8));
     CK(ensure(w->batch_hist, (hist_recs > 0 ? hist_recs : 1) * RBS_HIST_W * 8));
     CK(ensure(w->batch_sys, (size_t)nsys * sizeof(BatchSys)));
-    CK(ensure(w->batch_order, (size_t)nsys * sizeof(int32_t)));
+    CK(ensure(w->batch_order, (size_t)nsys * (sizeof(int32_t) + sizeof(int64_t))));
     CK(ensure(w->batch_out, (size_t)nsys * sizeof(BatchOut)));
     CK(ensure(w->batch_queue, 16));
     size_t woff = 0, hoff = 0;
@@ -754,12 +772,17 @@ extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_in
         B.b = S.b;
         B.x0 = S.x0;
         B.diag = S.jacobi_diag;
-        B.x = S.x;
         B.stride = (S.A.n + 31) / 32 * 32;
         B.work = (double *)w->batch_work.p + woff;
         woff += (size_t)B.stride * (S.variant == RBS_PIPELINED ? 17 : 9);
+        if (proxy) {
+            B.x = (double *)w->batch_work.p + woff;
+            woff += (size_t)B.stride;
+        } else {
+            B.x = S.x;
+        }
         B.tol = S.tol;
-        B.maxit = S.maxit;
+        B.maxit = proxy ? std::min(S.maxit, std::max(proxy_maxit[i], 1)) : S.maxit;
         B.variant = S.variant;
         const int cap = hists ? std::min(hists[i].cap, S.maxit) : 0;
         B.hist_cap = cap > 0 ? cap : 0;
@@ -772,28 +795,48 @@ extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_in
         return systems[a].A.nnz + systems[a].A.n > systems[b].A.nnz + systems[b].A.n;
     });
     const int nq = (int)order.size();
+    std::vector<int64_t> sizes((size_t)nq);
+    for (int q = 0; q < nq; q++) sizes[(size_t)q] = systems[order[(size_t)q]].A.n;
+    int32_t *d_order = (int32_t *)w->batch_order.p;
+    int64_t *d_sizes = (int64_t *)((char *)w->batch_order.p + (((size_t)nsys * sizeof(int32_t) + 7) / 8 * 8));
     CK(cudaMemcpyAsync(w->batch_sys.p, sys.data(), (size_t)nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
                        w->stream));
-    if (nq > 0)
-        CK(cudaMemcpyAsync(w->batch_order.p, order.data(), (size_t)nq * sizeof(int32_t), cudaMemcpyHostToDevice,
-                           w->stream));
+    if (nq > 0) {
+        CK(cudaMemcpyAsync(d_order, order.data(), (size_t)nq * sizeof(int32_t), cudaMemcpyHostToDevice, w->stream));
+        CK(cudaMemcpyAsync(d_sizes, sizes.data(), (size_t)nq * sizeof(int64_t), cudaMemcpyHostToDevice, w->stream));
+    }
     CK(cudaMemsetAsync(w->batch_out.p, 0, (size_t)nsys * sizeof(BatchOut), w->stream));
     CK(cudaMemsetAsync(w->batch_queue.p, 0, 16, w->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, w->stream));
+    }
     if (nq > 0) {
         // structure check and Jacobi set-up of the valid systems, then the solves
-        std::vector<BatchSys> packed;
-        packed.reserve((size_t)nq);
         CK(launch_batch_prepare((const BatchSys *)w->batch_sys.p, nsys, (BatchOut *)w->batch_out.p, w->stream));
-        const int clusters = std::max(1, std::min(batch_max_clusters(), nq));
-        CK(launch_batch((const BatchSys *)w->batch_sys.p, (const int32_t *)w->batch_order.p, nq,
-                        (unsigned *)w->batch_queue.p, (BatchOut *)w->batch_out.p, clusters, w->stream));
+        BatchSchedule b;
+        b.cluster = sched.cluster;
+        b.split = sched.split;
+        const int fit = batch_max_clusters(b.cluster);
+        if (fit < 1) return fail(RBS_EINVAL, "no cluster of this size fits on the device");
+        b.clusters = std::max(1, std::min(fit, nq));
+        CK(launch_batch((const BatchSys *)w->batch_sys.p, d_order, d_sizes, nq, (unsigned *)w->batch_queue.p,
+                        (BatchOut *)w->batch_out.p, b, w->stream));
+    }
+    if (ms) {
+        CK(cudaEventRecord(e1, w->stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
     }
     std::vector<BatchOut> out((size_t)nsys);
     CK(cudaMemcpyAsync(out.data(), w->batch_out.p, (size_t)nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost,
                        w->stream));
     CK(cudaStreamSynchronize(w->stream));
     int ret = RBS_OK;
-    hoff = 0;
     for (int i = 0; i < nsys; i++) {
         rbs_info &I = infos[i];
         const BatchOut &O = out[(size_t)i];
@@ -821,6 +864,86 @@ extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_in
     }
     if (ret) fail(ret, "one or more systems failed the argument or structure checks");
     return ret;
+}
+
+}  // namespace
+
+extern "C" int rbs_solve_batched_ex(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                                    const rbs_batch_schedule *sched, void *stream) {
+    if (nsys < 0 || (nsys > 0 && (!systems || !infos))) return fail(RBS_EINVAL, "bad batch arguments");
+    if (sched && !schedule_ok(*sched)) return fail(RBS_EINVAL, "bad batch schedule");
+    if (nsys == 0) return RBS_OK;
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    rbs_batch_schedule use = default_schedule();
+    if (sched) {
+        use = *sched;
+    } else {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(w->dev);
+        if (it != g_tuned.end()) use = it->second;
+    }
+    std::lock_guard<std::mutex> lk(w->mu);
+    return batch_solve(w, nsys, systems, infos, hists, use, nullptr, nullptr);
+}
+
+extern "C" int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                                 void *stream) {
+    return rbs_solve_batched_ex(nsys, systems, infos, hists, nullptr, stream);
+}
+
+extern "C" int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs_info *prev, int32_t proxy_iters,
+                              rbs_batch_schedule *best, void *stream) {
+    if (nsys < 1 || !systems || !best || proxy_iters < 1) return fail(RBS_EINVAL, "bad tuning arguments");
+    Workspace *w;
+    int rc = ws_get((cudaStream_t)stream, &w);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(w->mu);
+    // proxy iteration caps: a fixed number, or a fraction of a previous solve's
+    // counts so that the systems keep their relative costs
+    std::vector<int32_t> cap((size_t)nsys, proxy_iters);
+    if (prev) {
+        int32_t mx = 1;
+        for (int i = 0; i < nsys; i++) mx = std::max(mx, prev[i].iters);
+        for (int i = 0; i < nsys; i++)
+            cap[(size_t)i] = std::max(1, (int32_t)((int64_t)prev[i].iters * proxy_iters / mx));
+    }
+    // split candidates: quantiles of the system sizes
+    std::vector<int64_t> n;
+    for (int i = 0; i < nsys; i++) n.push_back(systems[i].A.n);
+    std::sort(n.begin(), n.end());
+    auto quant = [&](double f) { return n[(size_t)std::min<double>((double)n.size() - 1, f * (double)n.size())]; };
+    std::vector<int64_t> splits = {0, quant(0.5), quant(0.75), quant(0.9), n.back() + 1};
+    std::vector<rbs_info> infos((size_t)nsys);
+    rbs_batch_schedule top = default_schedule();
+    float top_ms = -1.f;
+    auto trial = [&](int cluster, int64_t split) -> int {
+        rbs_batch_schedule s = default_schedule();
+        s.cluster = cluster;
+        s.split = split;
+        if (batch_max_clusters(cluster) < 1) return RBS_OK;
+        float ms = 0.f;
+        int r = batch_solve(w, nsys, systems, infos.data(), nullptr, s, cap.data(), &ms);
+        if (r && r != RBS_EINVAL) return r;
+        if (top_ms < 0.f || ms < top_ms) {
+            top = s;
+            top_ms = ms;
+        }
+        return RBS_OK;
+    };
+    // cluster sizes at the median split, then every split for the best size
+    for (int c : {1, 2, 4, 8, 16})
+        if ((rc = trial(c, c == 1 ? 0 : splits[1]))) return rc;
+    const int bestc = top.cluster;
+    if (bestc > 1)
+        for (size_t k = 0; k < splits.size(); k++)
+            if (k != 1 && (rc = trial(bestc, splits[k]))) return rc;
+    top.ms = top_ms;
+    *best = top;
+    std::lock_guard<std::mutex> lk2(g_tuned_mu);
+    g_tuned[w->dev] = top;
+    return RBS_OK;
 }
 
 extern "C" int rbs_fpe_dot(const double *x, const double *y, int64_t n, double *out, int32_t *fell_back,

@@ -1,16 +1,21 @@
 // Batched solver: many independent systems in one persistent launch.
 //
-// Thread-block clusters of BC CTAs take systems from a queue (largest first)
-// and run a whole classic (Fig. 2) or pipelined (Fig. 4) solve each: the
-// system's rows are split across the cluster's CTAs, element-wise steps touch
-// only a CTA's own rows, the SpMV gathers x from the whole vector, and every
-// exact dot is reduced across the cluster through distributed shared memory.
-// Each CTA rounds the cluster-summed integers itself and runs the same scalar
-// recurrence on the same bits, so all CTAs of a cluster take the same
-// decisions and meet the same cluster barriers; no CTA ever spins on a flag.
+// The launch is made of thread-block clusters of C CTAs (C chosen at launch:
+// 1, 2, 4, 8 or 16). Systems come from a queue ordered largest first. While
+// the next system has at least `split` unknowns, a whole cluster solves it:
+// the rows are split across the cluster's CTAs, element-wise steps touch only a
+// CTA's own rows, the SpMV gathers x from the whole vector, and every exact dot
+// is reduced across the cluster through distributed shared memory. From the
+// first smaller system on, the cluster's CTAs work alone, each taking its own
+// systems from the queue and solving them with CTA barriers only, so small
+// systems do not pay for cluster barriers and every SM stays busy to the end.
+// Every group (cluster or CTA) rounds the group-summed integers itself and
+// runs the same scalar recurrence on the same bits, so all its CTAs take the
+// same decisions and meet the same barriers; no CTA ever spins on a flag.
 // Arithmetic, fma forms and readings are those of the per-step kernels, so a
-// system's result is bitwise the one rbs_solve gives.
+// system's result is bitwise the one rbs_solve gives, whatever the schedule.
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "kernels.cuh"
 #include "launch.h"
@@ -20,7 +25,7 @@ namespace cg = cooperative_groups;
 
 namespace rbs {
 
-constexpr int BC = 8;  // CTAs per cluster
+constexpr int BMAX = 16;  // most CTAs per cluster (non-portable size)
 constexpr int BQ = 4;  // exact-dot window placements
 
 enum Slot { S_R, S_R0, S_P, S_PH, S_S, S_Q, S_QH, S_Y, S_INVD, S_RH, S_W, S_WH, S_T, S_SH, S_Z, S_ZH, S_V };
@@ -55,35 +60,52 @@ __device__ __forceinline__ double spmv_row_l2(const CSRView &A, int64_t i, const
 
 struct ClusterRed {
     unsigned long long (*acc)[NL];  // this CTA's accumulators (shared)
-    long long (*red)[NL];           // cluster sums (shared)
+    long long (*red)[NL];           // group sums (shared)
     uint32_t *flags, *rflags;
     double *vals;
 };
 
-// Reduce K exact dots across the cluster; afterwards vals[0..K-1] hold the
-// rounded dots in every CTA and the accumulators are zero again.
+// The CTAs that solve one system together: the whole cluster, or one CTA.
+struct Grp {
+    cg::cluster_group *cl;  // null for a CTA working alone
+    unsigned rank, size;
+    __device__ __forceinline__ void sync() const {
+        if (cl) cl->sync();
+        else __syncthreads();
+    }
+};
+
+// Reduce K exact dots across the group; afterwards vals[0..K-1] hold the
+// rounded dots in every CTA of the group and the accumulators are zero again.
 template <int K>
-__device__ __forceinline__ void cluster_reduce(cg::cluster_group &cl, Win<BQ> (&win)[K], uint32_t (&fl)[K],
-                                               const ClusterRed &R) {
+__device__ __forceinline__ void group_reduce(const Grp &g, Win<BQ> (&win)[K], uint32_t (&fl)[K],
+                                             const ClusterRed &R) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
         warp_flush<BQ, FLUSH_SCRATCH>(win[k], R.acc[k]);
         if (fl[k]) atomicOr(&R.flags[k], fl[k]);
         fl[k] = 0u;
     }
-    cl.sync();
+    g.sync();
     for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) {
         long long sum = 0;
-        for (int r = 0; r < BC; r++)
-            sum += (long long)*cl.map_shared_rank(&R.acc[0][0] + idx, r);
+        if (g.cl) {
+            for (unsigned r = 0; r < g.size; r++) sum += (long long)*g.cl->map_shared_rank(&R.acc[0][0] + idx, r);
+        } else {
+            sum = (long long)(&R.acc[0][0])[idx];
+        }
         (&R.red[0][0])[idx] = sum;
     }
     if (threadIdx.x < K) {
         uint32_t f = 0u;
-        for (int r = 0; r < BC; r++) f |= *cl.map_shared_rank(R.flags + threadIdx.x, r);
+        if (g.cl) {
+            for (unsigned r = 0; r < g.size; r++) f |= *g.cl->map_shared_rank(R.flags + threadIdx.x, r);
+        } else {
+            f = R.flags[threadIdx.x];
+        }
         R.rflags[threadIdx.x] = f;
     }
-    cl.sync();
+    g.sync();
     for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) (&R.acc[0][0])[idx] = 0ull;
     if (threadIdx.x < K) {
         R.flags[threadIdx.x] = 0u;
@@ -101,11 +123,11 @@ struct SysView {
     double *hist;
 };
 
-__device__ __forceinline__ void sys_view(const BatchSys &S, unsigned rank, SysView &V) {
+__device__ __forceinline__ void sys_view(const BatchSys &S, const Grp &g, SysView &V) {
     V.A = CSRView{S.A.n, S.A.nnz, S.A.rowptr, S.A.col, S.A.val};
     V.n = S.A.n;
-    V.lo = V.n * (int64_t)rank / BC;
-    V.hi = V.n * (int64_t)(rank + 1) / BC;
+    V.lo = V.n * (int64_t)g.rank / g.size;
+    V.hi = V.n * (int64_t)(g.rank + 1) / g.size;
     for (int k = 0; k < 17; k++) V.v[k] = S.work + (int64_t)k * S.stride;
     V.x = S.x;
     V.b = S.b;
@@ -115,7 +137,7 @@ __device__ __forceinline__ void sys_view(const BatchSys &S, unsigned rank, SysVi
 
 #define OWN_ROWS(i) for (int64_t i = V.lo + threadIdx.x; i < V.hi; i += blockDim.x)
 
-__device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverState *st, const ClusterRed &R,
+__device__ void solve_classic(const Grp &cl, const SysView &V, SolverState *st, const ClusterRed &R,
                               bool &bad) {
     double *r = V.v[S_R], *r0 = V.v[S_R0], *p = V.v[S_P], *ph = V.v[S_PH], *s = V.v[S_S], *q = V.v[S_Q],
            *qh = V.v[S_QH], *y = V.v[S_Y], *invd = V.v[S_INVD], *x = V.x;
@@ -139,7 +161,7 @@ __device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverSta
         ph[i] = __dmul_rn(ri, invd[i]);
         exact_add<BQ, true>(w1[0], f1[0], R.acc[0], ri, ri);
     }
-    cluster_reduce<1>(cl, w1, f1, R);
+    group_reduce<1>(cl, w1, f1, R);
     if (threadIdx.x == 0) tail_cls_setup(st, R.vals);
     __syncthreads();
     for (int guard = 0; !st->done && guard <= st->maxit; guard++) {
@@ -148,7 +170,7 @@ __device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverSta
             s[i] = si;
             exact_add<BQ>(w1[0], f1[0], R.acc[0], r0[i], si);
         }
-        cluster_reduce<1>(cl, w1, f1, R);
+        group_reduce<1>(cl, w1, f1, R);
         if (threadIdx.x == 0) tail_cls_alpha(st, R.vals);
         __syncthreads();
         if (st->done) break;
@@ -165,7 +187,7 @@ __device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverSta
             exact_add<BQ>(w2[0], f2[0], R.acc[0], q[i], yi);
             exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
         }
-        cluster_reduce<2>(cl, w2, f2, R);
+        group_reduce<2>(cl, w2, f2, R);
         if (threadIdx.x == 0) tail_cls_omega(st, R.vals);
         __syncthreads();
         const double al = st->alpha, om = st->omega, nom = -om;
@@ -176,7 +198,7 @@ __device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverSta
             exact_add<BQ>(w2[0], f2[0], R.acc[0], r0[i], ri);
             exact_add<BQ, true>(w2[1], f2[1], R.acc[1], ri, ri);
         }
-        cluster_reduce<2>(cl, w2, f2, R);
+        group_reduce<2>(cl, w2, f2, R);
         if (threadIdx.x == 0) tail_cls_beta(st, R.vals, V.hist);
         __syncthreads();
         if (st->done) break;
@@ -190,7 +212,7 @@ __device__ void solve_classic(cg::cluster_group &cl, const SysView &V, SolverSta
     }
 }
 
-__device__ void solve_pipelined(cg::cluster_group &cl, const SysView &V, SolverState *st, const ClusterRed &R,
+__device__ void solve_pipelined(const Grp &cl, const SysView &V, SolverState *st, const ClusterRed &R,
                                 bool &bad) {
     double *r = V.v[S_R], *r0 = V.v[S_R0], *rh = V.v[S_RH], *w = V.v[S_W], *wh = V.v[S_WH], *t = V.v[S_T],
            *ph = V.v[S_PH], *s = V.v[S_S], *sh = V.v[S_SH], *z = V.v[S_Z], *zh = V.v[S_ZH], *v = V.v[S_V],
@@ -221,7 +243,7 @@ __device__ void solve_pipelined(cg::cluster_group &cl, const SysView &V, SolverS
         exact_add<BQ, true>(w2[0], f2[0], R.acc[0], r0i, r0i);
         exact_add<BQ>(w2[1], f2[1], R.acc[1], r0i, wi);
     }
-    cluster_reduce<2>(cl, w2, f2, R);
+    group_reduce<2>(cl, w2, f2, R);
     if (threadIdx.x == 0) tail_pipe_setup(st, R.vals);
     __syncthreads();
     if (!st->done) {
@@ -260,7 +282,7 @@ __device__ void solve_pipelined(cg::cluster_group &cl, const SysView &V, SolverS
             exact_add<BQ>(w2[0], f2[0], R.acc[0], qi, yi);
             exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
         }
-        cluster_reduce<2>(cl, w2, f2, R);  // also orders zhat for P2's gathers
+        group_reduce<2>(cl, w2, f2, R);  // also orders zhat for P2's gathers
         if (threadIdx.x == 0) tail_pipe_omega(st, R.vals);
         __syncthreads();
         OWN_ROWS(i) v[i] = spmv_row_l2(V.A, i, zh, bad);  // P2
@@ -283,7 +305,7 @@ __device__ void solve_pipelined(cg::cluster_group &cl, const SysView &V, SolverS
             exact_add<BQ>(w5[3], f5[3], R.acc[3], r0i, z[i]);
             exact_add<BQ, true>(w5[4], f5[4], R.acc[4], ri, ri);
         }
-        cluster_reduce<5>(cl, w5, f5, R);  // also orders what for P4's gathers
+        group_reduce<5>(cl, w5, f5, R);  // also orders what for P4's gathers
         if (threadIdx.x == 0) tail_pipe_beta(st, R.vals, V.hist);
         __syncthreads();
         if (st->done) break;
@@ -292,11 +314,51 @@ __device__ void solve_pipelined(cg::cluster_group &cl, const SysView &V, SolverS
     }
 }
 
-__global__ void __cluster_dims__(BC, 1, 1) __launch_bounds__(256)
-    k_batch(const BatchSys *__restrict__ sys, const int32_t *__restrict__ order, int nsys, unsigned *queue,
-            BatchOut *out) {
+// Solve one queued system (index qi of the order) as group g; rank 0 of the
+// group writes the outcome.
+__device__ __noinline__ void batch_solve_one(const Grp &g, const BatchSys *__restrict__ sys, const int32_t *__restrict__ order,
+                                int qi, BatchOut *out, SolverState &st, const ClusterRed &R, int &s_bad) {
+    const int si = order[qi];
+    const BatchSys &S = sys[si];
+    if (out[si].err) return;  // failed the structure check: same for every CTA of the group
+    if (threadIdx.x == 0) {
+        memset(&st, 0, sizeof st);
+        st.tol = S.tol;
+        st.maxit = S.maxit;
+        st.variant = S.variant;
+        st.hist_cap = g.rank == 0 ? S.hist_cap : 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    SysView V;
+    sys_view(S, g, V);
+    bool bad = false;
+    if (S.variant == RBS_PIPELINED) solve_pipelined(g, V, &st, R, bad);
+    else solve_classic(g, V, &st, R, bad);
+    if (bad) atomicOr(reinterpret_cast<unsigned *>(&s_bad), 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_bad) atomicOr(&out[si].err, 1u);
+        if (g.rank == 0) {
+            out[si].iters = st.iter;
+            out[si].status = st.status;
+            out[si].converged = (st.status == RBS_OK && !(st.tau > st.tau_max)) ? 1 : 0;
+            out[si].tau0 = st.tau0;
+            out[si].tau_final = st.tau;
+            out[si].rho0 = st.rho0;
+            out[si].tau_max = st.tau_max;
+            out[si].alpha0 = st.alpha0;
+            out[si].mu0 = st.mu0;
+        }
+    }
+}
+
+// sizes[q]: unknowns of the q-th queued system (non-increasing).
+__global__ void __launch_bounds__(256)
+    k_batch(const BatchSys *__restrict__ sys, const int32_t *__restrict__ order, const int64_t *__restrict__ sizes,
+            int nsys, int64_t split, unsigned *queue, BatchOut *out) {
     cg::cluster_group cl = cg::this_cluster();
-    const unsigned rank = cl.block_rank();
+    const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
     __shared__ int s_next;
     __shared__ SolverState st;
     __shared__ unsigned long long s_acc[5][NL];
@@ -308,58 +370,35 @@ __global__ void __cluster_dims__(BC, 1, 1) __launch_bounds__(256)
     if (threadIdx.x < 5) s_flags[threadIdx.x] = 0u;
     ClusterRed R{s_acc, s_red, s_flags, s_rflags, s_vals};
     cl.sync();  // every CTA of the cluster runs before any shared memory is touched remotely
-    for (int guard = 0; guard <= nsys; guard++) {
-        if (rank == 0 && threadIdx.x == 0) {
-            const int q = (int)atomicAdd(queue, 1u);
-            for (int r = 0; r < BC; r++) *cl.map_shared_rank(&s_next, r) = q;
-        }
-        cl.sync();
-        const int qi = s_next;
-        cl.sync();
-        if (qi >= nsys) break;
-        const int si = order[qi];
-        const BatchSys &S = sys[si];
-        if (out[si].err) continue;  // failed the structure check: same for every CTA
-        if (threadIdx.x == 0) {
-            memset(&st, 0, sizeof st);
-            st.tol = S.tol;
-            st.maxit = S.maxit;
-            st.variant = S.variant;
-            st.hist_cap = rank == 0 ? S.hist_cap : 0;
-            s_bad = 0;
-        }
-        __syncthreads();
-        SysView V;
-        sys_view(S, rank, V);
-        bool bad = false;
-        if (S.variant == RBS_PIPELINED) solve_pipelined(cl, V, &st, R, bad);
-        else solve_classic(cl, V, &st, R, bad);
-        if (bad) atomicOr(reinterpret_cast<unsigned *>(&s_bad), 1u);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (s_bad) atomicOr(&out[si].err, 1u);
-            if (rank == 0) {
-                BatchOut o = out[si];
-                o.iters = st.iter;
-                o.status = st.status;
-                o.converged = (st.status == RBS_OK && !(st.tau > st.tau_max)) ? 1 : 0;
-                o.tau0 = st.tau0;
-                o.tau_final = st.tau;
-                o.rho0 = st.rho0;
-                o.tau_max = st.tau_max;
-                o.alpha0 = st.alpha0;
-                o.mu0 = st.mu0;
-                out[si].iters = o.iters;
-                out[si].status = o.status;
-                out[si].converged = o.converged;
-                out[si].tau0 = o.tau0;
-                out[si].tau_final = o.tau_final;
-                out[si].rho0 = o.rho0;
-                out[si].tau_max = o.tau_max;
-                out[si].alpha0 = o.alpha0;
-                out[si].mu0 = o.mu0;
+    int first_small = -1;  // a small system the cluster pulled, solved by rank 0 alone
+    if (csize > 1) {
+        const Grp g{&cl, rank, csize};
+        for (int guard = 0; guard <= nsys; guard++) {
+            if (rank == 0 && threadIdx.x == 0) {
+                const int q = (int)atomicAdd(queue, 1u);
+                for (unsigned r = 0; r < csize; r++) *cl.map_shared_rank(&s_next, r) = q;
             }
+            cl.sync();
+            const int qi = s_next;
+            cl.sync();  // no remote access of the cluster's shared memory after this in the phase
+            if (qi >= nsys) break;
+            if (sizes[qi] < split) {
+                first_small = rank == 0 ? qi : -1;
+                break;
+            }
+            batch_solve_one(g, sys, order, qi, out, st, R, s_bad);
         }
+    }
+    // the CTAs now work alone: each takes its own systems from the queue
+    const Grp g1{nullptr, 0u, 1u};
+    if (first_small >= 0) batch_solve_one(g1, sys, order, first_small, out, st, R, s_bad);
+    for (int guard = 0; guard <= nsys; guard++) {
+        if (threadIdx.x == 0) s_next = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int qi = s_next;
+        __syncthreads();
+        if (qi >= nsys) break;
+        batch_solve_one(g1, sys, order, qi, out, st, R, s_bad);
     }
 }
 
@@ -408,27 +447,46 @@ cudaError_t launch_batch_prepare(const BatchSys *d_sys, int nsys, BatchOut *d_ou
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, int nsys, unsigned *d_queue,
-                         BatchOut *d_out, int clusters, cudaStream_t s) {
-    k_batch<<<clusters * BC, 256, 0, s>>>(d_sys, d_order, nsys, d_queue, d_out);
-    return cudaGetLastError();
+static cudaLaunchConfig_t batch_cfg(int clusters, int csize, cudaStream_t s, cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * csize), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    attr->id = cudaLaunchAttributeClusterDimension;
+    attr->val.clusterDim.x = (unsigned)csize;
+    attr->val.clusterDim.y = 1;
+    attr->val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
-int batch_max_clusters() {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(BC, 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
+static void allow_large_clusters() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaGetLastError();
+    });
+}
+
+cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, const int64_t *d_sizes, int nsys,
+                         unsigned *d_queue, BatchOut *d_out, BatchSchedule sched, cudaStream_t s) {
+    if (sched.cluster < 1 || sched.cluster > BMAX || (sched.cluster & (sched.cluster - 1)))
+        return cudaErrorInvalidValue;
+    allow_large_clusters();
     cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = BC;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg = batch_cfg(sched.clusters, sched.cluster, s, &attr);
+    return cudaLaunchKernelEx(&cfg, k_batch, d_sys, d_order, d_sizes, nsys, (int64_t)sched.split, d_queue, d_out);
+}
+
+int batch_max_clusters(int csize) {
+    allow_large_clusters();
+    cudaLaunchAttribute attr;
+    cudaLaunchConfig_t cfg = batch_cfg(1, csize, nullptr, &attr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, (void *)k_batch, &cfg) != cudaSuccess || n < 1) {
         cudaGetLastError();
-        n = 1;
+        n = 0;
     }
     return n;
 }

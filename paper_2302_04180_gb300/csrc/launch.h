@@ -107,9 +107,17 @@ struct BatchOut {
     double tau0, tau_final, rho0, tau_max, alpha0, mu0;
 };
 cudaError_t launch_batch_prepare(const BatchSys *d_sys, int nsys, BatchOut *d_out, cudaStream_t s);
-cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, int nsys, unsigned *d_queue,
-                         BatchOut *d_out, int clusters, cudaStream_t s);
-int batch_max_clusters();
+// Schedule of one batched launch: `clusters` clusters of `cluster` CTAs; a
+// queued system with at least `split` unknowns is solved by a whole cluster,
+// smaller ones by one CTA each.
+struct BatchSchedule {
+    int cluster, clusters;
+    int64_t split;
+};
+cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, const int64_t *d_sizes, int nsys,
+                         unsigned *d_queue, BatchOut *d_out, BatchSchedule sched, cudaStream_t s);
+// Clusters of `csize` CTAs that fit on the device at once (0 if none).
+int batch_max_clusters(int csize);
 
 // occupancy-derived persistent grid for the kernels of one kind
 int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout);

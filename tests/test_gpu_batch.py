@@ -93,3 +93,58 @@ def test_batch_reports_invalid_systems(dev, orc):
     assert res[3]["iters"] == 0 and res[3]["converged"] == 0
     assert res[4]["iters"] == 0 and res[4]["converged"] == 1
     assert (res[4]["x"] == 0).all()
+
+
+def _ref_solves(rbs, systems, work, maxit):
+    return [rbs.rbs_solve(sd["A"], sd["b"], tol=1e-8, maxit=maxit, variant=v) for sd, (A, v) in
+            zip(systems, work)]
+
+
+def _same_as(res, refs):
+    for r, s in zip(res, refs):
+        assert r["iters"] == s["iters"] and r["status"] == s["status"]
+        assert same_array(r["hist"], s["hist"])
+        assert same_array(r["x"].cpu().numpy(), s["x"].cpu().numpy())
+
+
+def test_batch_results_do_not_depend_on_the_schedule(dev):
+    import paper_2302_04180_gb300 as rbs
+    work = gen.batch_workload(24, seed=11, n_min=300, n_max=30000)
+    systems = [_device_system(rbs, dev, A, v, 1e-8, 1500) for A, v in work]
+    refs = _ref_solves(rbs, systems, work, 1500)
+    med = int(sorted(A.n for A, _ in work)[len(work) // 2])
+    for cluster, split in ((1, 0), (2, 0), (4, med), (8, 0), (8, med), (8, 1 << 40), (16, med)):
+        try:
+            res = rbs.rbs_solve_batched(systems, schedule={"cluster": cluster, "split": split})
+        except rbs.RbsError as e:
+            # a 16-CTA cluster needs the device's non-portable cluster size
+            assert cluster == 16 and e.code == rbs.RBS_EINVAL
+            continue
+        _same_as(res, refs)
+
+
+def test_batch_rejects_bad_schedule(dev):
+    import paper_2302_04180_gb300 as rbs
+    A, v = gen.batch_workload(1, seed=1, n_min=500, n_max=600)[0]
+    sd = _device_system(rbs, dev, A, v, 1e-8, 200)
+    with pytest.raises(rbs.RbsError) as e:
+        rbs.rbs_solve_batched([sd], schedule={"cluster": 3, "split": 0})
+    assert e.value.code == rbs.RBS_EINVAL
+
+
+def test_batch_tuner_picks_a_schedule_and_leaves_results_unchanged(dev):
+    import torch
+    import paper_2302_04180_gb300 as rbs
+    work = gen.batch_workload(32, seed=5, n_min=500, n_max=40000)
+    systems = [_device_system(rbs, dev, A, v, 1e-8, 2000) for A, v in work]
+    refs = _ref_solves(rbs, systems, work, 2000)
+    first = rbs.rbs_solve_batched(systems, history=False)
+    for sd in systems:
+        sd["x"].fill_(-7.0)
+    best = rbs.rbs_batch_tune(systems, prev=first, proxy_iters=16)
+    assert best["cluster"] in (1, 2, 4, 8, 16) and best["split"] >= 0 and best["ms"] > 0.0
+    for sd in systems:  # proxy solves write scratch, not the callers' x
+        assert bool((sd["x"] == -7.0).all())
+    res = rbs.rbs_solve_batched(systems)  # now under the tuned schedule
+    _same_as(res, refs)
+    torch.cuda.synchronize()
