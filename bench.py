@@ -391,7 +391,8 @@ def _serving(rbs, gen, dev, rates=(50.0, 150.0, 300.0), count=300, seed=3):
 
 
 def _kernel_micro(rbs, gen, dev):
-    """Standalone exact dot (2^27, cond 1e32) and SpMV (Poisson 128^3) GB/s."""
+    """Standalone exact dot (2^27, cond 1e32) and SpMV (Poisson 128^3, 27-point
+    e-type 159^3) GB/s."""
     import torch
     out = {}
 
@@ -422,6 +423,16 @@ def _kernel_micro(rbs, gen, dev):
     ms = timeit(lambda: rbs.rbs_spmv_csr(Ad, xv, yv))
     byt = 12 * A.nnz + 8 * (A.n + 1) + 16 * A.n
     out["spmv_poisson128"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9}
+    del Ad, xv, yv
+    # the 27-point e-type stencil at the paper's scalability size (159^3 =
+    # 4,019,679 unknowns, 27 nonzeros per interior row: long-span staging)
+    A = gen.stencil27(159)
+    Ad = rbs.to_device(A, dev)
+    xv = torch.from_numpy(gen.random_vector(A.n, 1)).to(dev)
+    yv = torch.empty_like(xv)
+    ms = timeit(lambda: rbs.rbs_spmv_csr(Ad, xv, yv))
+    byt = 12 * A.nnz + 8 * (A.n + 1) + 16 * A.n
+    out["spmv_stencil27_159"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9}
     return out
 
 

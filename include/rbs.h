@@ -314,6 +314,9 @@ int rbs_server_submit(rbs_server *srv, const rbs_system *system, int64_t *ticket
 int rbs_server_poll(rbs_server *srv, int64_t ticket, int32_t *done, rbs_info *info, double *latency_s,
                     double *queue_s);
 int rbs_server_wait(rbs_server *srv, int64_t ticket, rbs_info *info, double *latency_s, double *queue_s);
+/* (poll and wait: a request whose solve call failed as a whole -- not one of
+ * its systems -- reports that call's status in info->status, and
+ * rbs_last_error() then gives the call's message.) */
 int rbs_server_destroy(rbs_server *srv);
 
 /* ---- library control ---------------------------------------------------------- */
@@ -324,7 +327,8 @@ int rbs_stream_status(void *stream);
 int rbs_release(void);
 /* Launch-shape knobs for tuning and for configuration-independence tests.
  * Names: "exdot.grid", "exdot.block", "exdot.window" (0 = auto),
- * "spmv.block", "spmv.mode" (0 warp-staged rows, 1 one thread per row),
+ * "spmv.block", "spmv.mode" (0 auto: warp-staged rows, long-span staging when rows
+ * average more than 8 nonzeros; 1 one thread per row; 2 short; 3 long staging),
  * "vec.grid", "vec.block", "solve.check_every", "smem.carveout" (percent of
  * L1/shared storage for the staging kernels; default 75, -1 = driver default).
  * Results never depend on them. */

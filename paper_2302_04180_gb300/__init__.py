@@ -432,8 +432,9 @@ class RbsServer:
 
     def _result(self, ticket, info, lat, que):
         sd = self._keep.pop(ticket, None)
+        err = load().rbs_last_error().decode() if info.status != RBS_OK else ""
         return {"x": sd["x"] if sd else None, "iters": info.iters, "converged": info.converged,
-                "status": info.status, "latency_s": lat.value, "queue_s": que.value}
+                "status": info.status, "latency_s": lat.value, "queue_s": que.value, "error": err}
 
     def wait(self, ticket):
         info, lat, que = _Info(), C.c_double(), C.c_double()

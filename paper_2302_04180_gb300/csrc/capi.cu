@@ -51,6 +51,15 @@ std::atomic<int64_t> *param_slot(const char *name) {
     return nullptr;
 }
 
+// SpMV row schedule: knob spmv.mode 1 (one thread per row), 2 (warp-staged,
+// short spans) or 3 (warp-staged, long spans); 0 picks the staging from the
+// average row length (long spans above 8 nonzeros per row).
+int spmv_mode_for(int64_t n, int64_t nnz) {
+    const int64_t m = p_spmv_mode.load();
+    if (m == SPMV_MODE_ROW || m == SPMV_MODE_SHORT || m == SPMV_MODE_LONG) return (int)m;
+    return (n > 0 && nnz > 8 * n) ? SPMV_MODE_LONG : SPMV_MODE_SHORT;
+}
+
 int block_of(int64_t v, int def) {
     if (v <= 0) return def;
     int b = (int)(v > 256 ? 256 : v);
@@ -493,8 +502,9 @@ int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream) {
     CSRArgs a{A->n, A->nnz, A->rowptr, A->col, A->val};
     const int sb = block_of(p_spmv_block.load(), 256);
     const int carve = carveout_param();
-    Cfg c = grid_for(w, A->n, sb, spmv_blocks_per_sm(sb, carve));
-    c.mode = p_spmv_mode.load() == 1 ? 1 : 0;
+    const int mode = spmv_mode_for(A->n, A->nnz);
+    Cfg c = grid_for(w, A->n, sb, spmv_blocks_per_sm(sb, carve, mode));
+    c.mode = mode;
     c.carveout = carve;
     CK(launch_spmv(a, x, y, nullptr, &w->g->err, c, w->stream));
     return RBS_OK;
@@ -604,12 +614,13 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
     {
         const int vb = block_of(p_vec_block.load(), 256);
         const int carve = carveout_param();
-        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1, vb, carve);
+        const int smode = spmv_mode_for(n, nnz);
+        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1, vb, carve, smode);
         a.vec = grid_for(w, (n + 1) / 2, vb, bps);
         if (p_vec_grid.load() > 0) a.vec.grid = (int)p_vec_grid.load();
         const int sb = block_of(p_spmv_block.load(), 256);
-        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve));
-        a.spmv.mode = p_spmv_mode.load() == 1 ? 1 : 0;
+        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve, smode));
+        a.spmv.mode = smode;
         a.carveout = carveout_param();
         a.spmv.carveout = a.carveout;
         // window headroom: at most 2^20 products per thread per launch
@@ -758,7 +769,7 @@ int batch_solve(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_info 
     CK(ensure(w->batch_work, work_elems * 8));
     CK(ensure(w->batch_hist, (hist_recs > 0 ? hist_recs : 1) * RBS_HIST_W * 8));
     CK(ensure(w->batch_sys, (size_t)nsys * sizeof(BatchSys)));
-    CK(ensure(w->batch_order, (size_t)nsys * (sizeof(int32_t) + sizeof(int64_t))));
+    CK(ensure(w->batch_order, ((size_t)nsys * sizeof(int32_t) + 7) / 8 * 8 + (size_t)nsys * sizeof(int64_t)));
     CK(ensure(w->batch_out, (size_t)nsys * sizeof(BatchOut)));
     CK(ensure(w->batch_queue, 16));
     size_t woff = 0, hoff = 0;

@@ -55,22 +55,30 @@ constexpr unsigned ERR_TIMEOUT = 4u;  // a bounded wait on an asynchronous copy 
 // one lane with three bulk asynchronous copies (the span rounded out to whole
 // 16-byte units, never past the end of the arrays) that complete on the
 // buffer's mbarrier; any other chunk by per-lane 16-byte (or, unaligned,
-// element) asynchronous copies. Spans longer than SPMV_CAP (or, when CHECKED,
+// element) asynchronous copies. Spans longer than CAP (or, when CHECKED,
 // malformed row pointers) take the per-lane unstaged path. With CHECKED every
 // index is range-checked and a bad one reported (ERR_INDEX); without it the
 // caller has validated the structure (rowptr monotone from 0 to nnz, columns
 // in [0, n)). The arithmetic is exactly spmv_row's; only the memory schedule
 // differs. fn(row, y_row, z_row) runs in the owning lane (z_row = 0 without z).
 // All 32 lanes of every warp must enter; blocks have at most MAX_WARPS warps.
-// Kernels that also flush exact windows name SPMV_SCRATCH so that the flush
-// reuses the same shared buffer.
-constexpr int SPMV_CAP = 224;                           // 32 rows of a 7-point stencil
-constexpr int SPMV_VAL_OFF = 32 * 8;                    // z slice first
-constexpr int SPMV_COL_OFF = SPMV_VAL_OFF + (SPMV_CAP + 2) * 8;
-constexpr int SPMV_BUF = SPMV_COL_OFF + (SPMV_CAP + 8) * 4;  // 2992 bytes per buffer
-constexpr int SPMV_SCRATCH = 2 * SPMV_BUF;                   // per warp: two buffers
-static_assert(SPMV_VAL_OFF % 16 == 0 && SPMV_COL_OFF % 16 == 0 && SPMV_BUF % 16 == 0, "16-byte units");
-static_assert(SPMV_SCRATCH >= FLUSH_SCRATCH, "the flush reuses the staging buffers");
+// Kernels that also flush exact windows name SpmvLayout<CAP>::SCRATCH so that
+// the flush reuses the same shared buffer.
+// Staging layout of one chunk buffer for spans of at most CAP nonzeros: the
+// z slice (32 doubles), then val (CAP + 2 for the 16-byte rounding), then col
+// (CAP + 8); two buffers per warp. CAP 224 holds 32 rows of a 7-point stencil
+// (three 256-thread blocks per SM); CAP 1024 holds 32 rows of up to 32
+// nonzeros, e.g. the 27-point stencil (one block per SM).
+template <int CAP>
+struct SpmvLayout {
+    static constexpr int VAL_OFF = 32 * 8;
+    static constexpr int COL_OFF = VAL_OFF + (CAP + 2) * 8;
+    static constexpr int BUF = (COL_OFF + (CAP + 8) * 4 + 15) / 16 * 16;
+    static constexpr int SCRATCH = 2 * BUF;  // per warp
+    static_assert(COL_OFF % 16 == 0 && BUF >= COL_OFF + (CAP + 8) * 4, "16-byte units");
+    static_assert(SCRATCH >= FLUSH_SCRATCH, "the flush reuses the staging buffers");
+};
+constexpr int SPMV_CAP_SHORT = 224, SPMV_CAP_LONG = 1024;
 constexpr long long SPMV_WAIT_LIMIT = 1LL << 26;  // mbarrier polls before ERR_TIMEOUT
 
 enum : int { CHUNK_UNSTAGED = 0, CHUNK_LANES = 1, CHUNK_BULK = 2 };
@@ -127,7 +135,7 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
 // decide how it is staged and issue its copies into buffer `buf` (mbarrier
 // `bar` for bulk copies). Always commits one cp.async group, so group counting
 // stays uniform.
-template <bool CHECKED>
+template <bool CHECKED, int CAP>
 __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double *z, bool wide, bool bulk_ok,
                                                   int64_t rb, long long b, long long e, unsigned char *buf,
                                                   unsigned long long *bar) {
@@ -141,11 +149,12 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double
         const long long E = __shfl_sync(FULL, e, last);
         const long long span = E - B;
         c.B = B;
-        bool ok = span >= 0 && span <= SPMV_CAP;
+        using L = SpmvLayout<CAP>;
+        bool ok = span >= 0 && span <= CAP;
         if (CHECKED) ok = __all_sync(FULL, !live || (b >= B && e >= b && e <= E)) && ok && B >= 0 && E <= A.nnz;
         if (ok) {
-            double *sval = reinterpret_cast<double *>(buf + SPMV_VAL_OFF);
-            int32_t *scol = reinterpret_cast<int32_t *>(buf + SPMV_COL_OFF);
+            double *sval = reinterpret_cast<double *>(buf + L::VAL_OFF);
+            int32_t *scol = reinterpret_cast<int32_t *>(buf + L::COL_OFF);
             const long long va = spmv_va(B, wide), ca = spmv_ca(B, wide);
             const long long ve = (E + 1) & ~1LL, ce = (E + 3) & ~3LL;
             if (bulk_ok && last == 31 && ve <= A.nnz && ce <= A.nnz) {
@@ -191,7 +200,7 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double
     return c;
 }
 
-template <bool CHECKED, class F>
+template <bool CHECKED, int CAP, class F>
 __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x,
                                                const double *__restrict__ z, unsigned &err, F &&fn) {
     __shared__ __align__(8) unsigned long long s_bar[MAX_WARPS][2];
@@ -203,7 +212,8 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
     const unsigned ncol = A.n < 0x80000000LL ? (unsigned)A.n : 0x80000000u;
     const bool wide = ((reinterpret_cast<uintptr_t>(A.col) | reinterpret_cast<uintptr_t>(A.val)) & 15) == 0;
     const bool bulk_ok = wide && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
-    unsigned char *bufs = warp_scratch<SPMV_SCRATCH>();
+    using L = SpmvLayout<CAP>;
+    unsigned char *bufs = warp_scratch<L::SCRATCH>();
     unsigned long long *bars = s_bar[wid];
     if (lane == 0) {
         mbar_init(bars);
@@ -223,12 +233,12 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
     };
     long long b0, e0, b1, e1, b2, e2;
     rowptrs(rb, b0, e0);
-    SpmvChunk c0 = spmv_prepare<CHECKED>(A, z, wide, bulk_ok, rb, b0, e0, bufs, bars);
+    SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, z, wide, bulk_ok, rb, b0, e0, bufs, bars);
     rowptrs(rb + step, b1, e1);
     int cur = 0;
     for (; rb < A.n; rb += step) {
-        const SpmvChunk c1 =
-            spmv_prepare<CHECKED>(A, z, wide, bulk_ok, rb + step, b1, e1, bufs + (cur ^ 1) * SPMV_BUF, bars + (cur ^ 1));
+        const SpmvChunk c1 = spmv_prepare<CHECKED, CAP>(A, z, wide, bulk_ok, rb + step, b1, e1,
+                                                       bufs + (cur ^ 1) * L::BUF, bars + (cur ^ 1));
         rowptrs(rb + 2 * step, b2, e2);
         if (c0.how == CHUNK_BULK) {
             long long spins = 0;
@@ -247,11 +257,11 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
         if (r < A.n) {
             double acc = 0.0, zr = 0.0;
             if (c0.how != CHUNK_UNSTAGED) {
-                const unsigned char *buf = bufs + cur * SPMV_BUF;
+                const unsigned char *buf = bufs + cur * L::BUF;
                 const int32_t *scol =
-                    reinterpret_cast<const int32_t *>(buf + SPMV_COL_OFF) + (b0 - spmv_ca(c0.B, wide));
+                    reinterpret_cast<const int32_t *>(buf + L::COL_OFF) + (b0 - spmv_ca(c0.B, wide));
                 const double *sval =
-                    reinterpret_cast<const double *>(buf + SPMV_VAL_OFF) + (b0 - spmv_va(c0.B, wide));
+                    reinterpret_cast<const double *>(buf + L::VAL_OFF) + (b0 - spmv_va(c0.B, wide));
                 const int len = (int)(e0 - b0);
                 unsigned cmax = 0u;
                 for (int k0 = 0; k0 < len; k0 += 8) {
@@ -304,14 +314,14 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
-// Row traversal of y = A x with epilogue fn(row, y_row, z_row): mode 0
-// warp-staged, mode 1 one thread per row. Same bits either way. z may be null.
-// Error bits (ERR_*) accumulate in err.
-template <bool CHECKED, class F>
+// Row traversal of y = A x with epilogue fn(row, y_row, z_row): mode 1 one
+// thread per row, any other mode warp-staged with spans of up to CAP nonzeros.
+// Same bits either way. z may be null. Error bits (ERR_*) accumulate in err.
+template <bool CHECKED, int CAP, class F>
 __device__ __forceinline__ void spmv_each(const CSRView &A, const double *__restrict__ x,
                                           const double *__restrict__ z, int mode, unsigned &err, F &&fn) {
-    if (mode == 0) {
-        spmv_warp_rows<CHECKED>(A, x, z, err, fn);
+    if (mode != 1) {
+        spmv_warp_rows<CHECKED, CAP>(A, x, z, err, fn);
     } else {
         bool bad = false;
         for (int64_t i = gtid(); i < A.n; i += gstride()) fn(i, spmv_row(A, i, x, bad), z ? z[i] : 0.0);

@@ -157,12 +157,13 @@ cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, doubl
 // 1) in a grid-stride loop. CHECKED: every index is range-checked (the
 // standalone product); without it the solver has validated the structure at
 // set-up. With a solver state, the kernel is a no-op once the solver stopped.
-template <bool CHECKED>
-__global__ void __launch_bounds__(256, 3) k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y,
-                                              const SolverState *st, unsigned *err, int mode) {
+template <bool CHECKED, int CAP>
+__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3)
+    k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y, const SolverState *st, unsigned *err,
+           int mode) {
     if (st && st->done) return;
     unsigned eb = 0u;
-    spmv_each<CHECKED>(A, x, nullptr, mode, eb, [&](int64_t i, double v, double) { y[i] = v; });
+    spmv_each<CHECKED, CAP>(A, x, nullptr, mode, eb, [&](int64_t i, double v, double) { y[i] = v; });
     if (eb) atomicOr(err, eb);
 }
 
@@ -179,17 +180,23 @@ static void spmv_carveout(int c) {
     }
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && applied[dev] != c) {
-        cudaFuncSetAttribute(k_spmv<true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-        cudaFuncSetAttribute(k_spmv<false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+        cudaFuncSetAttribute(k_spmv<true, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+        cudaFuncSetAttribute(k_spmv<false, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+        const int cl = c < 0 ? c : 100;  // the long-row kernels need (nearly) all of it
+        cudaFuncSetAttribute(k_spmv<true, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
+        cudaFuncSetAttribute(k_spmv<false, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
         cudaGetLastError();
         applied[dev] = c;
     }
 }
 
-int spmv_blocks_per_sm(int block, int carveout) {
+int spmv_blocks_per_sm(int block, int carveout, int mode) {
     spmv_carveout(carveout);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true>, block, 0) != cudaSuccess || nb < 1) {
+    const cudaError_t e =
+        mode == SPMV_MODE_LONG ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true, SPMV_CAP_LONG>, block, 0)
+                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true, SPMV_CAP_SHORT>, block, 0);
+    if (e != cudaSuccess || nb < 1) {
         cudaGetLastError();
         nb = 1;
     }
@@ -199,8 +206,11 @@ int spmv_blocks_per_sm(int block, int carveout) {
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s) {
     spmv_carveout(cfg.carveout);
-    if (st) k_spmv<false><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
-    else k_spmv<true><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    const bool lng = cfg.mode == SPMV_MODE_LONG;
+    if (st && lng) k_spmv<false, SPMV_CAP_LONG><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    else if (st) k_spmv<false, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    else if (lng) k_spmv<true, SPMV_CAP_LONG><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    else k_spmv<true, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
     return cudaGetLastError();
 }
 

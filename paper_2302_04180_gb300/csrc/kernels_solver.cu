@@ -72,19 +72,19 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
 }
 
 // K1: s = A phat, <r0, s>
-template <class R>
-__global__ void __launch_bounds__(256, 3) k_cls_k1(Ctx c) {
+template <class R, int CAP>
+__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     unsigned eb = 0u;
-    spmv_each<false>(c.A, c.ph, c.r0, c.spmv_mode, eb, [&](int64_t i, double si, double r0) {
+    spmv_each<false, CAP>(c.A, c.ph, c.r0, c.spmv_mode, eb, [&](int64_t i, double si, double r0) {
         c.s[i] = si;
         red.add(0, r0, si);
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SPMV_SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
+    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
 }
 
 // K2: q = fma(-alpha, s, r), qhat = q * invd
@@ -110,20 +110,20 @@ __global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
 }
 
 // K3: y = A qhat, <q, y>, <y, y>
-template <class R>
-__global__ void __launch_bounds__(256, 3) k_cls_k3(Ctx c) {
+template <class R, int CAP>
+__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     unsigned eb = 0u;
-    spmv_each<false>(c.A, c.qh, c.q, c.spmv_mode, eb, [&](int64_t i, double yi, double qi) {
+    spmv_each<false, CAP>(c.A, c.qh, c.q, c.spmv_mode, eb, [&](int64_t i, double yi, double qi) {
         c.y[i] = yi;
         red.add(0, qi, yi);
         red.add_sq(1, yi);
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SPMV_SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
+    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
 }
 
 // K4: x = fma(omega, qhat, fma(alpha, phat, x)), r = fma(-omega, y, q), <r0,r>, <r,r>
@@ -205,12 +205,12 @@ __global__ void __launch_bounds__(256) k_pipe_setup1(Ctx c) {
 }
 
 // set-up 2: w = A rhat, what = w * invd, <r0,r>, <r0,w> -> alpha0
-template <class R>
-__global__ void __launch_bounds__(256) k_pipe_setup2(Ctx c) {
+template <class R, int CAP>
+__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_pipe_setup2(Ctx c) {
     R red;
     red.init();
     unsigned eb = 0u;
-    spmv_each<false>(c.A, c.rh, c.r0, c.spmv_mode, eb, [&](int64_t i, double wi, double r0) {
+    spmv_each<false, CAP>(c.A, c.rh, c.r0, c.spmv_mode, eb, [&](int64_t i, double wi, double r0) {
         c.w[i] = wi;
         c.wh[i] = __dmul_rn(wi, c.invd[i]);
         red.add_sq(0, r0);  // r = r0 at set-up
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k_pipe_setup2(Ctx c) {
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SPMV_SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
+    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
 }
 
 // P1: S1-S4 (copies at iteration 0), S5-S7, S9; <q,y>, <y,y> -> omega
@@ -320,7 +320,10 @@ static cudaError_t setup_t(const SolverArgs &a, int variant, cudaStream_t s, Ker
         TIMED(PK_SETUP, (k_cls_setup<R1><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
     } else {
         TIMED(PK_SETUP, (k_pipe_setup1<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
-        TIMED(PK_SETUP, (k_pipe_setup2<R2><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        if (a.spmv.mode == SPMV_MODE_LONG)
+            TIMED(PK_SETUP, (k_pipe_setup2<R2, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        else
+            TIMED(PK_SETUP, (k_pipe_setup2<R2, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         TIMED(PK_SETUP, (launch_spmv(a.A, a.v.wh, a.v.t, a.st, a.err, a.spmv, s)));
     }
     return cudaGetLastError();
@@ -330,9 +333,12 @@ template <class R1, class R2, class R5>
 static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *tm) {
     Ctx c = make_ctx(a);
     if (variant == RBS_CLASSIC) {
-        TIMED(PK_SPMV_DOT, (k_cls_k1<R1><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        const bool lng = a.spmv.mode == SPMV_MODE_LONG;
+        if (lng) TIMED(PK_SPMV_DOT, (k_cls_k1<R1, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        else TIMED(PK_SPMV_DOT, (k_cls_k1<R1, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k2<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
-        TIMED(PK_SPMV_DOT, (k_cls_k3<R2><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        if (lng) TIMED(PK_SPMV_DOT, (k_cls_k3<R2, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        else TIMED(PK_SPMV_DOT, (k_cls_k3<R2, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k4<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k5<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
     } else {
@@ -349,10 +355,15 @@ static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, Kern
 // the SpMV live on L1 hits, so the split is a tuning knob, not a maximum.
 template <class R1, class R2, class R5>
 static void prefer_shared(int c) {
-    cudaFuncSetAttribute(k_cls_k1<R1>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-    cudaFuncSetAttribute(k_cls_k3<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_cls_k1<R1, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_cls_k3<R2, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
     cudaFuncSetAttribute(k_cls_k4<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-    cudaFuncSetAttribute(k_pipe_setup2<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(k_pipe_setup2<R2, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    // the long-row kernels need (nearly) all of it for their staging buffers
+    const int cl = c < 0 ? c : 100;
+    cudaFuncSetAttribute(k_cls_k1<R1, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
+    cudaFuncSetAttribute(k_cls_k3<R2, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
+    cudaFuncSetAttribute(k_pipe_setup2<R2, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
     cudaFuncSetAttribute(k_pipe_p1<R2>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
     cudaFuncSetAttribute(k_pipe_p3<R5>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
     cudaGetLastError();
@@ -402,16 +413,20 @@ cudaError_t launch_set_cond(cudaGraphConditionalHandle h, SolverState *st, cudaS
     return cudaGetLastError();
 }
 
-int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout) {
+int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout, int spmv_mode) {
     apply_carveout(dot_mode, carveout);
-    if (which == 0 && variant == RBS_PIPELINED) return spmv_blocks_per_sm(block, carveout);
+    if (which == 0 && variant == RBS_PIPELINED) return spmv_blocks_per_sm(block, carveout, spmv_mode);
+    const bool lng = spmv_mode == SPMV_MODE_LONG;
     int nb = 0, nb2 = 0;
     cudaError_t e = cudaSuccess;
     if (dot_mode == RBS_DOT_PLAIN) {
         if (which == 0) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<PlainR<1>>, block, 0);
+            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<PlainR<1>, SPMV_CAP_LONG>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<PlainR<1>, SPMV_CAP_SHORT>, block, 0);
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<PlainR<2>>, block, 0);
+                e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<PlainR<2>, SPMV_CAP_LONG>, block, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<PlainR<2>, SPMV_CAP_SHORT>, block,
+                                                                        0);
             nb = nb2 < nb ? nb2 : nb;
         } else if (variant == RBS_PIPELINED) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, block, 0);
@@ -419,9 +434,12 @@ int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int ca
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<PlainR<2>>, block, 0);
         }
     } else if (which == 0) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<ExactR<1, SQ>>, block, 0);
+        e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<ExactR<1, SQ>, SPMV_CAP_LONG>, block, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<ExactR<1, SQ>, SPMV_CAP_SHORT>, block, 0);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<ExactR<2, SQ>>, block, 0);
+            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<ExactR<2, SQ>, SPMV_CAP_LONG>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<ExactR<2, SQ>, SPMV_CAP_SHORT>, block,
+                                                                    0);
         nb = nb2 < nb ? nb2 : nb;
     } else if (variant == RBS_PIPELINED) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, block, 0);

@@ -19,10 +19,14 @@ struct CSRArgs {
     const double *val;
 };
 
+// SpMV row schedules (Cfg::mode): one thread per row, warp-staged chunks of
+// up to SPMV_CAP_SHORT or SPMV_CAP_LONG nonzeros.
+enum : int { SPMV_MODE_ROW = 1, SPMV_MODE_SHORT = 2, SPMV_MODE_LONG = 3 };
+
 struct Cfg {
     int grid = 0;
     int block = 256;
-    int mode = 0;       // SpMV row schedule: 0 warp-staged, 1 thread per row
+    int mode = 2;       // SpMV row schedule (SPMV_MODE_*)
     int carveout = -1;  // shared-memory carveout percent, -1 = driver default
 };
 
@@ -120,9 +124,9 @@ cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, const in
 int batch_max_clusters(int csize);
 
 // occupancy-derived persistent grid for the kernels of one kind
-int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout);
+int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout, int spmv_mode);
 // Resident blocks per SM of the standalone SpMV kernel at this block size and
 // shared-memory carveout (applies the carveout first).
-int spmv_blocks_per_sm(int block, int carveout);
+int spmv_blocks_per_sm(int block, int carveout, int mode);
 
 }  // namespace rbs

@@ -17,6 +17,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -38,6 +39,7 @@ struct Request {
     rbs_info info;
     bool done;
     int batch_size;
+    std::string error;  // message of a call that failed as a whole
 };
 
 int64_t state_bytes(const rbs_system &s) {
@@ -98,20 +100,28 @@ struct Server {
             }
             if (mine.empty()) continue;
             infos.assign(mine.size(), rbs_info{});
+            int rc;
             if (mine.size() == 1 && sys[0].A.n >= solo_n) {
                 const rbs_system &q = sys[0];
                 rbs_opts o{};
-                rbs_solve_ex(&q.A, q.b, q.x0, q.jacobi_diag, q.tol, q.maxit, q.variant, &o, q.x, &infos[0],
-                             nullptr, nullptr, stream);
+                rc = rbs_solve_ex(&q.A, q.b, q.x0, q.jacobi_diag, q.tol, q.maxit, q.variant, &o, q.x, &infos[0],
+                                  nullptr, nullptr, stream);
             } else {
-                rbs_solve_batched((int32_t)mine.size(), sys.data(), infos.data(), nullptr, stream);
+                rc = rbs_solve_batched((int32_t)mine.size(), sys.data(), infos.data(), nullptr, stream);
             }
+            // a call that failed as a whole leaves its requests unsolved: they
+            // report its status (per-system statuses are already in infos)
+            const char *msg = rc ? rbs_last_error() : "";
             {
                 std::lock_guard<std::mutex> lk(mu);
                 const auto now = Clock::now();
                 for (size_t i = 0; i < mine.size(); i++) {
                     Request &r = reqs[mine[i]];
                     r.info = infos[i];
+                    if (rc && r.info.status == RBS_OK && r.info.iters == 0) {
+                        r.info.status = rc;
+                        r.error = msg;
+                    }
                     r.finished = now;
                     r.done = true;
                     r.batch_size = (int)mine.size();
@@ -173,6 +183,7 @@ int rbs_server_submit(rbs_server *srv, const rbs_system *system, int64_t *ticket
 }
 
 static void fill_result(const Request &r, rbs_info *info, double *latency_s, double *queue_s) {
+    if (!r.error.empty()) set_error(r.info.status, r.error.c_str());
     if (info) *info = r.info;
     if (latency_s) *latency_s = std::chrono::duration<double>(r.finished - r.submitted).count();
     if (queue_s) *queue_s = std::chrono::duration<double>(r.started - r.submitted).count();

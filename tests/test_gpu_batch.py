@@ -142,6 +142,7 @@ def test_batch_tuner_picks_a_schedule_and_leaves_results_unchanged(dev):
     for sd in systems:
         sd["x"].fill_(-7.0)
     best = rbs.rbs_batch_tune(systems, prev=first, proxy_iters=16)
+    print("tuned schedule", best)
     assert best["cluster"] in (1, 2, 4, 8, 16) and best["split"] >= 0 and best["ms"] > 0.0
     for sd in systems:  # proxy solves write scratch, not the callers' x
         assert bool((sd["x"] == -7.0).all())

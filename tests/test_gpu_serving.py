@@ -43,7 +43,7 @@ def test_mixed_stream_matches_solo_solves(orc, workers, max_batch, budget, solo_
         results = [(srv.wait(t), p) for t, p in tickets]
     for r, p in results:
         alone = pool[p][4]
-        assert r["status"] == alone["status"] == 0
+        assert r["status"] == alone["status"] == 0, r.get("error")
         assert r["iters"] == alone["iters"]
         assert same_array(r["x"].cpu().numpy(), alone["x"].cpu().numpy())
         assert r["latency_s"] >= r["queue_s"] >= 0.0

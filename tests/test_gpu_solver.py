@@ -90,8 +90,8 @@ def test_launch_shape_and_chunk_independence(rbs, dev, orc):
     o = orc.solve(A, orc.spmv(A, np.ones(A.n)), tol=1e-10, maxit=500, variant=0)
     carve = rbs.rbs_get_param("smem.carveout")
     for vg, vb, sb, ce, lm, sm, co in ((0, 0, 0, 0, 0, 0, 75), (0, 0, 0, 0, 1, 1, -1), (1, 32, 32, 1, 1, 0, 100),
-                                       (7, 128, 64, 3, 0, 1, 50), (500, 256, 256, 50, 1, 0, 0),
-                                       (152, 64, 128, 0, 0, 1, 75)):
+                                       (7, 128, 64, 3, 0, 1, 50), (500, 256, 256, 50, 1, 2, 0),
+                                       (152, 64, 128, 0, 0, 3, 75), (0, 0, 0, 5, 1, 3, 100)):
         rbs.rbs_set_param("spmv.mode", sm)
         rbs.rbs_set_param("smem.carveout", co)
         rbs.rbs_set_param("vec.grid", vg)

@@ -37,7 +37,7 @@ def test_random_csr(rbs, dev, orc, n, mr, empty, dup):
     x = gen.random_vector(n, 3) * 10.0 ** gen.random_vector(n, 3, 9, -100, 100)
     x[::5] = -0.0
     ref = orc.spmv(A, x)
-    for mode in (0, 1):  # long spans (mr=40) also exercise the staged path's fallback
+    for mode in (0, 1, 2, 3):  # long spans (mr=40) also exercise the staged path's fallback
         rbs.rbs_set_param("spmv.mode", mode)
         assert same_array(_spmv(rbs, dev, A, x), ref), mode
     rbs.rbs_set_param("spmv.mode", 0)
@@ -58,7 +58,7 @@ def test_poisson_128_full_size(rbs, dev, orc):
     assert A.n == 2097152 and A.nnz == 14581760
     x = gen.random_vector(A.n, 6)
     ref = orc.spmv(A, x)
-    for mode in (0, 1):
+    for mode in (0, 1, 2, 3):
         rbs.rbs_set_param("spmv.mode", mode)
         for block in (0, 64, 256):
             rbs.rbs_set_param("spmv.block", block)

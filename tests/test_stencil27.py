@@ -48,13 +48,22 @@ def test_gpu_e_type_and_banded_parity(orc, variant):
     import torch
     dev = cuda_device()
     import paper_2302_04180_gb300 as rbs
-    for A in (gen.stencil27(20), gen.banded(20000, 60)):
-        Ad = rbs.to_device(A, dev)
-        x = gen.random_vector(A.n, 4)
-        assert same_array(rbs.rbs_spmv_csr(Ad, torch.from_numpy(x).to(dev)).cpu().numpy(), orc.spmv(A, x))
-        b = orc.spmv(A, np.ones(A.n))
-        g = rbs.rbs_solve(Ad, torch.from_numpy(b).to(dev), tol=1e-10, maxit=400, variant=variant)
-        o = orc.solve(A, b, tol=1e-10, maxit=400, variant=variant)
-        assert g["iters"] == o["iters"] and g["status"] == o["status"]
-        assert same_array(g["hist"], o["hist"])
-        assert same_array(g["x"].cpu().numpy(), o["x"])
+    # spmv.mode 0 picks the long-span staging for these rows (27 and 121
+    # nonzeros); 2 forces the short spans (every chunk then takes the per-lane
+    # path), 1 one thread per row
+    try:
+        for A in (gen.stencil27(20), gen.banded(20000, 60), gen.banded(20001, 13)):
+            Ad = rbs.to_device(A, dev)
+            x = gen.random_vector(A.n, 4)
+            b = orc.spmv(A, np.ones(A.n))
+            o = orc.solve(A, b, tol=1e-10, maxit=400, variant=variant)
+            for mode in (0, 1, 2):
+                rbs.rbs_set_param("spmv.mode", mode)
+                assert same_array(rbs.rbs_spmv_csr(Ad, torch.from_numpy(x).to(dev)).cpu().numpy(),
+                                  orc.spmv(A, x)), mode
+                g = rbs.rbs_solve(Ad, torch.from_numpy(b).to(dev), tol=1e-10, maxit=400, variant=variant)
+                assert g["iters"] == o["iters"] and g["status"] == o["status"]
+                assert same_array(g["hist"], o["hist"])
+                assert same_array(g["x"].cpu().numpy(), o["x"])
+    finally:
+        rbs.rbs_set_param("spmv.mode", 0)
