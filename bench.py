@@ -343,7 +343,12 @@ def _batched(rbs, gen, dev):
     res, dt = timed({"cluster": best["cluster"], "split": best["split"]})
     same = all(a["iters"] == b["iters"] and bool(torch.equal(a["x"], x)) for a, b, x in zip(res, res0, x0s))
     its = sum(r["iters"] for r in res)
+    # algorithmic bytes of the whole batch: per iteration 2 SpMV (12 nnz each)
+    # plus the fused vector passes, 216 n bytes classic / 352 n pipelined
+    alg = sum(r["iters"] * (24 * A.nnz + (352 if v else 216) * A.n) for r, (A, v) in zip(res, work))
+    hbm, _ = _peaks()
     return {"systems": len(systems), "unknowns": int(sum(A.n for A, _ in work)),
+            "alg_bytes": int(alg), "achieved_GB/s": alg / dt / 1e9, "frac_of_hbm": alg / dt / 1e9 / hbm,
             "seconds": dt, "systems_per_s": len(systems) / dt, "iters_per_s": its / dt,
             "total_iters": its, "converged": int(sum(r["converged"] for r in res)),
             "schedule": {"cluster": best["cluster"], "split": best["split"]},

@@ -18,6 +18,7 @@ struct CSRView {
 // One CSR row in stored order, starting from +0.0, each step one fma rounded
 // to nearest even (Sec. 4.1 SpMV with the fma rule of Sec. 3.3). Every index
 // is checked; a bad one is skipped and reported through `bad`.
+template <bool L2X = false>
 __device__ __forceinline__ double spmv_row(const CSRView &A, int64_t i, const double *__restrict__ x,
                                            bool &bad) {
     const int64_t b = A.rowptr[i], e = A.rowptr[i + 1];
@@ -32,7 +33,7 @@ __device__ __forceinline__ double spmv_row(const CSRView &A, int64_t i, const do
             bad = true;
             continue;
         }
-        acc = fma(A.val[k], __ldg(x + c), acc);
+        acc = fma(A.val[k], L2X ? __ldcg(x + c) : __ldg(x + c), acc);
     }
     return acc;
 }
@@ -136,15 +137,15 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
 // `bar` for bulk copies). Always commits one cp.async group, so group counting
 // stays uniform.
 template <bool CHECKED, int CAP>
-__device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double *z, bool wide, bool bulk_ok,
-                                                  int64_t rb, long long b, long long e, unsigned char *buf,
-                                                  unsigned long long *bar) {
+__device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t r_end, const double *z, bool wide,
+                                                  bool bulk_ok, bool z_bulk, int64_t rb, long long b, long long e,
+                                                  unsigned char *buf, unsigned long long *bar) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     SpmvChunk c{0, CHUNK_UNSTAGED};
-    if (rb < A.n) {
-        const bool live = rb + lane < A.n;
-        const int last = (int)((A.n - 1 - rb) < 31 ? (A.n - 1 - rb) : 31);
+    if (rb < r_end) {
+        const bool live = rb + lane < r_end;
+        const int last = (int)((r_end - 1 - rb) < 31 ? (r_end - 1 - rb) : 31);
         const long long B = __shfl_sync(FULL, b, 0);
         const long long E = __shfl_sync(FULL, e, last);
         const long long span = E - B;
@@ -161,15 +162,19 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double
                 c.how = CHUNK_BULK;
                 if (lane == 0) {
                     const unsigned vbytes = (unsigned)(ve - va) * 8u, cbytes = (unsigned)(ce - ca) * 4u;
-                    const unsigned zbytes = z ? 256u : 0u;
+                    const unsigned zbytes = z && z_bulk ? 256u : 0u;
                     // earlier generic-proxy reads of this buffer happen before
                     // the bulk copies overwrite it
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                     mbar_arrive_expect_tx(bar, vbytes + cbytes + zbytes);
                     if (vbytes) bulk_copy_g2s(sval, A.val + va, vbytes, bar);
                     if (cbytes) bulk_copy_g2s(scol, A.col + ca, cbytes, bar);
-                    if (z) bulk_copy_g2s(buf, z + rb, 256u, bar);
+                    if (zbytes) bulk_copy_g2s(buf, z + rb, 256u, bar);
                 }
+                // a z written earlier in the same kernel is copied by the lanes
+                // (generic proxy), so that the earlier writes are seen
+                if (z && !z_bulk && live)
+                    __pipeline_memcpy_async(reinterpret_cast<double *>(buf) + lane, z + rb + lane, 8);
             } else {
                 c.how = CHUNK_LANES;
                 if (wide) {
@@ -200,18 +205,23 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, const double
     return c;
 }
 
-template <bool CHECKED, int CAP, class F>
-__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x,
-                                               const double *__restrict__ z, unsigned &err, F &&fn) {
+// Rows [r_begin, r_end) in chunks of 32, chunk k taken by warp k mod nwarps
+// (this warp is number `warp` of nwarps). L2X: x is read through L2 only
+// (ld.global.cg), for an x that other blocks write in the same kernel; z_bulk:
+// z may be fetched by the bulk copy (it is not written in the same kernel).
+template <bool CHECKED, int CAP, bool L2X, class F>
+__device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int64_t r_end, int64_t warp,
+                                          int64_t nwarps, const double *__restrict__ x,
+                                          const double *__restrict__ z, bool z_bulk, unsigned &err, F &&fn) {
     __shared__ __align__(8) unsigned long long s_bar[MAX_WARPS][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5) * 32;
-    int64_t rb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * 32;
+    const int64_t step = nwarps * 32;
+    int64_t rb = r_begin + warp * 32;
     // valid columns are [0, ncol): with CHECKED the largest column of a row is
     // tested once, and every gather stays in range
     const unsigned ncol = A.n < 0x80000000LL ? (unsigned)A.n : 0x80000000u;
     const bool wide = ((reinterpret_cast<uintptr_t>(A.col) | reinterpret_cast<uintptr_t>(A.val)) & 15) == 0;
-    const bool bulk_ok = wide && (reinterpret_cast<uintptr_t>(z) & 15) == 0;
+    const bool bulk_ok = wide && (!z_bulk || (reinterpret_cast<uintptr_t>(z) & 15) == 0);
     using L = SpmvLayout<CAP>;
     unsigned char *bufs = warp_scratch<L::SCRATCH>();
     unsigned long long *bars = s_bar[wid];
@@ -226,18 +236,18 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
         const int64_t r = r0 + lane;
         b = 0;
         e = 0;
-        if (r0 < A.n && r < A.n) {
+        if (r0 < r_end && r < r_end) {
             b = A.rowptr[r];
             e = A.rowptr[r + 1];
         }
     };
     long long b0, e0, b1, e1, b2, e2;
     rowptrs(rb, b0, e0);
-    SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, z, wide, bulk_ok, rb, b0, e0, bufs, bars);
+    SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, rb, b0, e0, bufs, bars);
     rowptrs(rb + step, b1, e1);
     int cur = 0;
-    for (; rb < A.n; rb += step) {
-        const SpmvChunk c1 = spmv_prepare<CHECKED, CAP>(A, z, wide, bulk_ok, rb + step, b1, e1,
+    for (; rb < r_end; rb += step) {
+        const SpmvChunk c1 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, rb + step, b1, e1,
                                                        bufs + (cur ^ 1) * L::BUF, bars + (cur ^ 1));
         rowptrs(rb + 2 * step, b2, e2);
         if (c0.how == CHUNK_BULK) {
@@ -249,12 +259,11 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
                 }
             }
             parity ^= 1u << cur;
-        } else {
-            __pipeline_wait_prior(1);  // chunk rb's copies have landed
         }
+        __pipeline_wait_prior(1);  // chunk rb's per-lane copies have landed
         __syncwarp();
         const int64_t r = rb + lane;
-        if (r < A.n) {
+        if (r < r_end) {
             double acc = 0.0, zr = 0.0;
             if (c0.how != CHUNK_UNSTAGED) {
                 const unsigned char *buf = bufs + cur * L::BUF;
@@ -277,9 +286,9 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
                                 // a bad column is reported and its gather clamped
                                 // into range (the call fails; the value is moot)
                                 cmax = max(cmax, cidx);
-                                xv[j] = __ldg(x + min(cidx, ncol - 1u));
+                                xv[j] = L2X ? __ldcg(x + min(cidx, ncol - 1u)) : __ldg(x + min(cidx, ncol - 1u));
                             } else {
-                                xv[j] = __ldg(x + cidx);
+                                xv[j] = L2X ? __ldcg(x + cidx) : __ldg(x + cidx);
                             }
                         }
                     }
@@ -291,7 +300,7 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
                 if (z) zr = reinterpret_cast<const double *>(buf)[lane];
             } else {
                 bool bad = false;
-                acc = spmv_row(A, r, x, bad);
+                acc = spmv_row<L2X>(A, r, x, bad);
                 if (bad) err |= ERR_INDEX;
                 if (z) zr = z[r];
             }
@@ -307,8 +316,16 @@ __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *_
     }
     __pipeline_wait_prior(0);
     // a bulk chunk prepared past the end is never waited for: there is none,
-    // since prepare stages nothing for rb >= n
+    // since prepare stages nothing for rb >= r_end
     __syncwarp();
+}
+
+// The whole matrix over the grid: every warp of every block.
+template <bool CHECKED, int CAP, class F>
+__device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x,
+                                               const double *__restrict__ z, unsigned &err, F &&fn) {
+    spmv_rows<CHECKED, CAP, false>(A, 0, A.n, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                   (int64_t)gridDim.x * (blockDim.x >> 5), x, z, true, err, fn);
 }
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }

@@ -137,6 +137,47 @@ __device__ __forceinline__ void sys_view(const BatchSys &S, const Grp &g, SysVie
 
 #define OWN_ROWS(i) for (int64_t i = V.lo + threadIdx.x; i < V.hi; i += blockDim.x)
 
+template <int N>
+struct Vals {
+    double v[N];
+};
+
+// This CTA's rows, two per thread per pass: ld(i) returns the values row i
+// needs and st(i, vals) computes and stores; both rows' loads are issued
+// before the first store, so twice the bytes are in flight per thread.
+template <class LD, class ST>
+__device__ __forceinline__ void own_rows2(const SysView &V, LD &&ld, ST &&st) {
+    const int64_t bd = blockDim.x;
+    for (int64_t i0 = V.lo + threadIdx.x; i0 < V.hi; i0 += 2 * bd) {
+        const int64_t i1 = i0 + bd;
+        const bool h1 = i1 < V.hi;
+        const auto a = ld(i0);
+        decltype(ld(i0)) b{};
+        if (h1) b = ld(i1);
+        st(i0, a);
+        if (h1) st(i1, b);
+    }
+}
+
+// The same, one row per thread per pass (the pipelined kernels' phases read up
+// to 13 vectors: two rows of them would not fit in registers).
+template <class LD, class ST>
+__device__ __forceinline__ void own_rows1(const SysView &V, LD &&ld, ST &&st) {
+    for (int64_t i = V.lo + threadIdx.x; i < V.hi; i += blockDim.x) st(i, ld(i));
+}
+
+// y = A x over this CTA's rows with the warp-staged SpMV: x through L2 (other
+// CTAs of the group wrote it in this kernel), z (nullable) staged by the lanes
+// (written earlier in this kernel), col and val by bulk copies.
+// fn(row, y_row, z_row) runs in the lane that owns the row.
+template <class F>
+__device__ __forceinline__ void group_spmv(const SysView &V, const double *x, const double *z, bool &bad,
+                                           F &&fn) {
+    unsigned eb = 0u;
+    spmv_rows<true, SPMV_CAP_SHORT, true>(V.A, V.lo, V.hi, threadIdx.x >> 5, blockDim.x >> 5, x, z, false, eb, fn);
+    if (eb) bad = true;
+}
+
 __device__ void solve_classic(const Grp &cl, const SysView &V, SolverState *st, const ClusterRed &R,
                               bool &bad) {
     double *r = V.v[S_R], *r0 = V.v[S_R0], *p = V.v[S_P], *ph = V.v[S_PH], *s = V.v[S_S], *q = V.v[S_Q],
@@ -165,49 +206,53 @@ __device__ void solve_classic(const Grp &cl, const SysView &V, SolverState *st, 
     if (threadIdx.x == 0) tail_cls_setup(st, R.vals);
     __syncthreads();
     for (int guard = 0; !st->done && guard <= st->maxit; guard++) {
-        OWN_ROWS(i) {  // K1
-            const double si = spmv_row_l2(V.A, i, ph, bad);
+        group_spmv(V, ph, r0, bad, [&](int64_t i, double si, double r0i) {  // K1
             s[i] = si;
-            exact_add<BQ>(w1[0], f1[0], R.acc[0], r0[i], si);
-        }
+            exact_add<BQ>(w1[0], f1[0], R.acc[0], r0i, si);
+        });
         group_reduce<1>(cl, w1, f1, R);
         if (threadIdx.x == 0) tail_cls_alpha(st, R.vals);
         __syncthreads();
         if (st->done) break;
         const double na = -st->alpha;
-        OWN_ROWS(i) {  // K2
-            const double qi = fma(na, s[i], r[i]);
-            q[i] = qi;
-            qh[i] = __dmul_rn(qi, invd[i]);
-        }
+        own_rows2(
+            V, [&](int64_t i) { return Vals<3>{{s[i], r[i], invd[i]}}; },
+            [&](int64_t i, const Vals<3> &a) {  // K2
+                const double qi = fma(na, a.v[0], a.v[1]);
+                q[i] = qi;
+                qh[i] = __dmul_rn(qi, a.v[2]);
+            });
         cl.sync();
-        OWN_ROWS(i) {  // K3
-            const double yi = spmv_row_l2(V.A, i, qh, bad);
+        group_spmv(V, qh, q, bad, [&](int64_t i, double yi, double qi) {  // K3
             y[i] = yi;
-            exact_add<BQ>(w2[0], f2[0], R.acc[0], q[i], yi);
+            exact_add<BQ>(w2[0], f2[0], R.acc[0], qi, yi);
             exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
-        }
+        });
         group_reduce<2>(cl, w2, f2, R);
         if (threadIdx.x == 0) tail_cls_omega(st, R.vals);
         __syncthreads();
         const double al = st->alpha, om = st->omega, nom = -om;
-        OWN_ROWS(i) {  // K4
-            x[i] = fma(om, qh[i], fma(al, ph[i], x[i]));
-            const double ri = fma(nom, y[i], q[i]);
-            r[i] = ri;
-            exact_add<BQ>(w2[0], f2[0], R.acc[0], r0[i], ri);
-            exact_add<BQ, true>(w2[1], f2[1], R.acc[1], ri, ri);
-        }
+        own_rows2(
+            V, [&](int64_t i) { return Vals<6>{{qh[i], ph[i], x[i], y[i], q[i], r0[i]}}; },
+            [&](int64_t i, const Vals<6> &a) {  // K4
+                x[i] = fma(om, a.v[0], fma(al, a.v[1], a.v[2]));
+                const double ri = fma(nom, a.v[3], a.v[4]);
+                r[i] = ri;
+                exact_add<BQ>(w2[0], f2[0], R.acc[0], a.v[5], ri);
+                exact_add<BQ, true>(w2[1], f2[1], R.acc[1], ri, ri);
+            });
         group_reduce<2>(cl, w2, f2, R);
         if (threadIdx.x == 0) tail_cls_beta(st, R.vals, V.hist);
         __syncthreads();
         if (st->done) break;
         const double be = st->beta;
-        OWN_ROWS(i) {  // K5
-            const double pi = fma(be, fma(nom, s[i], p[i]), r[i]);
-            p[i] = pi;
-            ph[i] = __dmul_rn(pi, invd[i]);
-        }
+        own_rows2(
+            V, [&](int64_t i) { return Vals<4>{{s[i], p[i], r[i], invd[i]}}; },
+            [&](int64_t i, const Vals<4> &a) {  // K5
+                const double pi = fma(be, fma(nom, a.v[0], a.v[1]), a.v[2]);
+                p[i] = pi;
+                ph[i] = __dmul_rn(pi, a.v[3]);
+            });
         cl.sync();
     }
 }
@@ -235,81 +280,106 @@ __device__ void solve_pipelined(const Grp &cl, const SysView &V, SolverState *st
         rh[i] = __dmul_rn(ri, invd[i]);
     }
     cl.sync();
-    OWN_ROWS(i) {
-        const double wi = spmv_row_l2(V.A, i, rh, bad);
+    group_spmv(V, rh, r0, bad, [&](int64_t i, double wi, double r0i) {
         w[i] = wi;
         wh[i] = __dmul_rn(wi, invd[i]);
-        const double r0i = r0[i];
         exact_add<BQ, true>(w2[0], f2[0], R.acc[0], r0i, r0i);
         exact_add<BQ>(w2[1], f2[1], R.acc[1], r0i, wi);
-    }
+    });
     group_reduce<2>(cl, w2, f2, R);
     if (threadIdx.x == 0) tail_pipe_setup(st, R.vals);
     __syncthreads();
     if (!st->done) {
-        OWN_ROWS(i) t[i] = spmv_row_l2(V.A, i, wh, bad);
+        group_spmv(V, wh, nullptr, bad, [&](int64_t i, double ti, double) { t[i] = ti; });
         cl.sync();
     }
     for (int guard = 0; !st->done && guard <= st->maxit; guard++) {
         const double al = st->alpha, nal = -al, be = st->beta, nom = -st->omega;
         const bool first = st->iter == 0;
-        OWN_ROWS(i) {  // P1: S1-S7, S9
-            double phi, si, shi, zi;
-            const double rhi = rh[i], wi = w[i], whi = wh[i], ti = t[i];
-            if (first) {
-                phi = rhi;
-                si = wi;
-                shi = whi;
-                zi = ti;
-            } else {
-                const double ph0 = ph[i], s0 = s[i], sh0 = sh[i], z0 = z[i], zh0 = zh[i], v0 = v[i];
-                phi = fma(be, fma(nom, sh0, ph0), rhi);
-                si = fma(be, fma(nom, z0, s0), wi);
-                shi = fma(be, fma(nom, zh0, sh0), whi);
-                zi = fma(be, fma(nom, v0, z0), ti);
-            }
-            const double qi = fma(nal, si, r[i]);
-            const double qhi = fma(nal, shi, rhi);
-            const double yi = fma(nal, zi, wi);
-            ph[i] = phi;
-            s[i] = si;
-            sh[i] = shi;
-            z[i] = zi;
-            q[i] = qi;
-            qh[i] = qhi;
-            y[i] = yi;
-            zh[i] = __dmul_rn(zi, invd[i]);
-            exact_add<BQ>(w2[0], f2[0], R.acc[0], qi, yi);
-            exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
-        }
+        own_rows1(
+            V,
+            [&](int64_t i) {
+                Vals<12> a;
+                a.v[0] = rh[i];
+                a.v[1] = w[i];
+                a.v[2] = wh[i];
+                a.v[3] = t[i];
+                a.v[4] = r[i];
+                a.v[5] = invd[i];
+                if (!first) {
+                    a.v[6] = ph[i];
+                    a.v[7] = s[i];
+                    a.v[8] = sh[i];
+                    a.v[9] = z[i];
+                    a.v[10] = zh[i];
+                    a.v[11] = v[i];
+                }
+                return a;
+            },
+            [&](int64_t i, const Vals<12> &a) {  // P1: S1-S7, S9
+                const double rhi = a.v[0], wi = a.v[1], whi = a.v[2], ti = a.v[3];
+                double phi, si, shi, zi;
+                if (first) {
+                    phi = rhi;
+                    si = wi;
+                    shi = whi;
+                    zi = ti;
+                } else {
+                    const double ph0 = a.v[6], s0 = a.v[7], sh0 = a.v[8], z0 = a.v[9], zh0 = a.v[10],
+                                 v0 = a.v[11];
+                    phi = fma(be, fma(nom, sh0, ph0), rhi);
+                    si = fma(be, fma(nom, z0, s0), wi);
+                    shi = fma(be, fma(nom, zh0, sh0), whi);
+                    zi = fma(be, fma(nom, v0, z0), ti);
+                }
+                const double qi = fma(nal, si, a.v[4]);
+                const double qhi = fma(nal, shi, rhi);
+                const double yi = fma(nal, zi, wi);
+                ph[i] = phi;
+                s[i] = si;
+                sh[i] = shi;
+                z[i] = zi;
+                q[i] = qi;
+                qh[i] = qhi;
+                y[i] = yi;
+                zh[i] = __dmul_rn(zi, a.v[5]);
+                exact_add<BQ>(w2[0], f2[0], R.acc[0], qi, yi);
+                exact_add<BQ, true>(w2[1], f2[1], R.acc[1], yi, yi);
+            });
         group_reduce<2>(cl, w2, f2, R);  // also orders zhat for P2's gathers
         if (threadIdx.x == 0) tail_pipe_omega(st, R.vals);
         __syncthreads();
-        OWN_ROWS(i) v[i] = spmv_row_l2(V.A, i, zh, bad);  // P2
+        group_spmv(V, zh, nullptr, bad, [&](int64_t i, double vi, double) { v[i] = vi; });  // P2
         cl.sync();
         const double om = st->omega, nom2 = -om;
-        OWN_ROWS(i) {  // P3: S12-S15, S17
-            const double qhi = qh[i], yi = y[i], qi = q[i];
-            x[i] = fma(om, qhi, fma(al, ph[i], x[i]));
-            const double ri = fma(nom2, yi, qi);
-            const double rhi = fma(nom2, fma(nal, zh[i], wh[i]), qhi);
-            const double wi = fma(nom2, fma(nal, v[i], t[i]), yi);
-            r[i] = ri;
-            rh[i] = rhi;
-            w[i] = wi;
-            wh[i] = __dmul_rn(wi, invd[i]);
-            const double r0i = r0[i];
-            exact_add<BQ>(w5[0], f5[0], R.acc[0], r0i, ri);
-            exact_add<BQ>(w5[1], f5[1], R.acc[1], r0i, wi);
-            exact_add<BQ>(w5[2], f5[2], R.acc[2], r0i, s[i]);
-            exact_add<BQ>(w5[3], f5[3], R.acc[3], r0i, z[i]);
-            exact_add<BQ, true>(w5[4], f5[4], R.acc[4], ri, ri);
-        }
+        own_rows1(
+            V,
+            [&](int64_t i) {
+                return Vals<13>{{qh[i], y[i], q[i], x[i], ph[i], zh[i], wh[i], v[i], t[i], invd[i], r0[i], s[i],
+                                 z[i]}};
+            },
+            [&](int64_t i, const Vals<13> &a) {  // P3: S12-S15, S17
+                const double qhi = a.v[0], yi = a.v[1], qi = a.v[2];
+                x[i] = fma(om, qhi, fma(al, a.v[4], a.v[3]));
+                const double ri = fma(nom2, yi, qi);
+                const double rhi = fma(nom2, fma(nal, a.v[5], a.v[6]), qhi);
+                const double wi = fma(nom2, fma(nal, a.v[7], a.v[8]), yi);
+                r[i] = ri;
+                rh[i] = rhi;
+                w[i] = wi;
+                wh[i] = __dmul_rn(wi, a.v[9]);
+                const double r0i = a.v[10];
+                exact_add<BQ>(w5[0], f5[0], R.acc[0], r0i, ri);
+                exact_add<BQ>(w5[1], f5[1], R.acc[1], r0i, wi);
+                exact_add<BQ>(w5[2], f5[2], R.acc[2], r0i, a.v[11]);
+                exact_add<BQ>(w5[3], f5[3], R.acc[3], r0i, a.v[12]);
+                exact_add<BQ, true>(w5[4], f5[4], R.acc[4], ri, ri);
+            });
         group_reduce<5>(cl, w5, f5, R);  // also orders what for P4's gathers
         if (threadIdx.x == 0) tail_pipe_beta(st, R.vals, V.hist);
         __syncthreads();
         if (st->done) break;
-        OWN_ROWS(i) t[i] = spmv_row_l2(V.A, i, wh, bad);  // P4
+        group_spmv(V, wh, nullptr, bad, [&](int64_t i, double ti, double) { t[i] = ti; });  // P4
         cl.sync();
     }
 }
@@ -354,7 +424,7 @@ __device__ __noinline__ void batch_solve_one(const Grp &g, const BatchSys *__res
 }
 
 // sizes[q]: unknowns of the q-th queued system (non-increasing).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
     k_batch(const BatchSys *__restrict__ sys, const int32_t *__restrict__ order, const int64_t *__restrict__ sizes,
             int nsys, int64_t split, unsigned *queue, BatchOut *out) {
     cg::cluster_group cl = cg::this_cluster();
@@ -465,6 +535,8 @@ static void allow_large_clusters() {
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_batch, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        // the SpMV staging buffers take most of a CTA's shared memory
+        cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaGetLastError();
     });
 }
