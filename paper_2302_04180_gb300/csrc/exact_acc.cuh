@@ -119,6 +119,42 @@ __device__ __forceinline__ void win_place_add(Win<Q> &W, const uint32_t (&u)[5],
     add8_carry(W.w, v, SIGNED ? (m & 1u) : 0u);
 }
 
+// win_place_add for windows anchored top-aligned (products of the anchor's
+// limb land at q = Q - 1): with Q = 4 the placements q = 2, 3 take the first
+// select level only and a branch picks the word layout, so the common case of
+// products within two limbs skips the second level (a branch that is uniform
+// across the warp on well-scaled data; divergent warps run both layouts, which
+// costs about what the second select level does).
+template <int Q>
+__device__ __forceinline__ void win_place_add_top(Win<Q> &W, const uint32_t (&u)[5], int q, uint32_t m) {
+    if (Q != 4) {
+        win_place_add<Q, true>(W, u, q, m);
+        return;
+    }
+    uint32_t x[5], t[6], v[8];
+#pragma unroll
+    for (int k = 0; k < 5; k++) x[k] = u[k] ^ m;
+    const bool b1 = (q & 1) != 0;
+    t[0] = b1 ? m : x[0];
+    t[1] = b1 ? x[0] : x[1];
+    t[2] = b1 ? x[1] : x[2];
+    t[3] = b1 ? x[2] : x[3];
+    t[4] = b1 ? x[3] : x[4];
+    t[5] = b1 ? x[4] : m;
+    if (q & 2) {
+        v[0] = m;
+        v[1] = m;
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k + 2] = t[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; k++) v[k] = t[k];
+        v[6] = m;
+        v[7] = m;
+    }
+    add8_carry(W.w, v, m & 1u);
+}
+
 // Add the window into the block accumulator as carry-save limbs: words 0..6
 // unsigned, word 7 the signed top of the two's complement value.
 template <int Q>
@@ -244,10 +280,10 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
     shift5(p0, p1, p2, p3, (uint32_t)pos & 31u, u);
     const int q = L - H.a;
     if ((unsigned)q < (unsigned)Q) {
-        win_place_add<Q, true>(H, u, q, m);
+        win_place_add_top<Q>(H, u, q, m);
         return;
     }
-    const int back = Q >= 2 ? Q - 2 : 0;
+    const int back = Q - 1;  // top-aligned: the anchoring product at q = Q - 1
     if (q >= Q) {
         if (H.a != WIN_EMPTY) {
             win_flush<Q>(Lw, sacc);
@@ -256,18 +292,18 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
 #pragma unroll
         for (int k = 0; k < 8; k++) H.w[k] = 0u;
         H.a = L - back < 0 ? 0 : L - back;
-        win_place_add<Q, true>(H, u, L - H.a, m);
+        win_place_add_top<Q>(H, u, L - H.a, m);
         return;
     }
     const int ql = L - Lw.a;
     if ((unsigned)ql < (unsigned)Q) {
-        win_place_add<Q, true>(Lw, u, ql, m);
+        win_place_add_top<Q>(Lw, u, ql, m);
         return;
     }
     if (ql >= Q) {
         win_flush<Q>(Lw, sacc);
         Lw.a = L - back < 0 ? 0 : L - back;
-        win_place_add<Q, true>(Lw, u, L - Lw.a, m);
+        win_place_add_top<Q>(Lw, u, L - Lw.a, m);
         return;
     }
     smem_deposit(sacc, u, L, m);
