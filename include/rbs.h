@@ -330,7 +330,11 @@ int rbs_release(void);
  * "spmv.block", "spmv.mode" (0 auto: warp-staged rows, long-span staging when rows
  * average more than 8 nonzeros; 1 one thread per row; 2 short; 3 long staging),
  * "vec.grid", "vec.block", "solve.check_every", "smem.carveout" (percent of
- * L1/shared storage for the staging kernels; default 75, -1 = driver default).
+ * L1/shared storage for the staging kernels; default 75, -1 = driver default);
+ * "test.stall_staging" (1: a test mode of the bounded device-side wait --
+ * the staged SpMV announces its bulk copies without issuing them and gives up
+ * after 64 polls, reads those rows from global memory instead, and the call
+ * reports RBS_ETIMEOUT; results do not change).
  * Results never depend on them. */
 int rbs_set_param(const char *name, int64_t value);
 int64_t rbs_get_param(const char *name);

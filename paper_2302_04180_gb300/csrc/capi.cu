@@ -35,7 +35,7 @@ int cuda_fail(cudaError_t e, const char *what) {
 
 // ---- knobs -------------------------------------------------------------------------
 std::atomic<int64_t> p_exdot_grid{0}, p_exdot_block{0}, p_exdot_window{0}, p_spmv_block{0},
-    p_vec_grid{0}, p_vec_block{0}, p_check_every{0}, p_spmv_mode{0}, p_carveout{75};
+    p_vec_grid{0}, p_vec_block{0}, p_check_every{0}, p_spmv_mode{0}, p_carveout{75}, p_test_stall{0};
 
 std::atomic<int64_t> *param_slot(const char *name) {
     if (!name) return nullptr;
@@ -48,6 +48,7 @@ std::atomic<int64_t> *param_slot(const char *name) {
     if (!strcmp(name, "solve.check_every")) return &p_check_every;
     if (!strcmp(name, "spmv.mode")) return &p_spmv_mode;
     if (!strcmp(name, "smem.carveout")) return &p_carveout;
+    if (!strcmp(name, "test.stall_staging")) return &p_test_stall;
     return nullptr;
 }
 
@@ -56,8 +57,9 @@ std::atomic<int64_t> *param_slot(const char *name) {
 // average row length (long spans above 8 nonzeros per row).
 int spmv_mode_for(int64_t n, int64_t nnz) {
     const int64_t m = p_spmv_mode.load();
-    if (m == SPMV_MODE_ROW || m == SPMV_MODE_SHORT || m == SPMV_MODE_LONG) return (int)m;
-    return (n > 0 && nnz > 8 * n) ? SPMV_MODE_LONG : SPMV_MODE_SHORT;
+    int mode = (n > 0 && nnz > 8 * n) ? SPMV_MODE_LONG : SPMV_MODE_SHORT;
+    if (m == SPMV_MODE_ROW || m == SPMV_MODE_SHORT || m == SPMV_MODE_LONG) mode = (int)m;
+    return mode | (p_test_stall.load() ? SPMV_TEST_STALL : 0);
 }
 
 int block_of(int64_t v, int def) {
@@ -503,7 +505,7 @@ int rbs_spmv_csr(const rbs_csr *A, const double *x, double *y, void *stream) {
     const int sb = block_of(p_spmv_block.load(), 256);
     const int carve = carveout_param();
     const int mode = spmv_mode_for(A->n, A->nnz);
-    Cfg c = grid_for(w, A->n, sb, spmv_blocks_per_sm(sb, carve, mode));
+    Cfg c = grid_for(w, A->n, sb, spmv_blocks_per_sm(sb, carve, mode & SPMV_MODE_MASK));
     c.mode = mode;
     c.carveout = carve;
     CK(launch_spmv(a, x, y, nullptr, &w->g->err, c, w->stream));
@@ -615,11 +617,11 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         const int vb = block_of(p_vec_block.load(), 256);
         const int carve = carveout_param();
         const int smode = spmv_mode_for(n, nnz);
-        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1, vb, carve, smode);
+        const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1, vb, carve, smode & SPMV_MODE_MASK);
         a.vec = grid_for(w, (n + 1) / 2, vb, bps);
         if (p_vec_grid.load() > 0) a.vec.grid = (int)p_vec_grid.load();
         const int sb = block_of(p_spmv_block.load(), 256);
-        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve, smode));
+        a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve, smode & SPMV_MODE_MASK));
         a.spmv.mode = smode;
         a.carveout = carveout_param();
         a.spmv.carveout = a.carveout;

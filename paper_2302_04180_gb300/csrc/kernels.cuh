@@ -4,6 +4,7 @@
 
 #include <cuda_pipeline.h>
 
+#include "launch.h"
 #include "reduce.cuh"
 
 namespace rbs {
@@ -80,7 +81,13 @@ struct SpmvLayout {
     static_assert(SCRATCH >= FLUSH_SCRATCH, "the flush reuses the staging buffers");
 };
 constexpr int SPMV_CAP_SHORT = 224, SPMV_CAP_LONG = 1024;
-constexpr long long SPMV_WAIT_LIMIT = 1LL << 26;  // mbarrier polls before ERR_TIMEOUT
+constexpr long long SPMV_WAIT_LIMIT = 1LL << 17;  // polls of at most ~10 us: ~1.3 s before ERR_TIMEOUT
+
+// Test mode of the bounded wait (bit SPMV_TEST_STALL of the SpMV mode, a
+// kernel argument): the issuing lane announces a chunk's bulk copies on the
+// mbarrier without issuing them, and the wait gives up after
+// SPMV_TEST_WAIT_LIMIT polls, so that the timeout path runs.
+constexpr long long SPMV_TEST_WAIT_LIMIT = 64;  // (SPMV_MODE_MASK, SPMV_TEST_STALL: launch.h)
 
 enum : int { CHUNK_UNSTAGED = 0, CHUNK_LANES = 1, CHUNK_BULK = 2 };
 
@@ -112,14 +119,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+// One bounded poll: returns once the phase of `parity` has completed or after
+// at most about 10 us of suspension.
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(10000u)
         : "memory");
     return ok != 0u;
 }
@@ -138,8 +147,8 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsign
 // stays uniform.
 template <bool CHECKED, int CAP>
 __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t r_end, const double *z, bool wide,
-                                                  bool bulk_ok, bool z_bulk, int64_t rb, long long b, long long e,
-                                                  unsigned char *buf, unsigned long long *bar) {
+                                                  bool bulk_ok, bool z_bulk, bool skip_bulk, int64_t rb, long long b,
+                                                  long long e, unsigned char *buf, unsigned long long *bar) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     SpmvChunk c{0, CHUNK_UNSTAGED};
@@ -167,9 +176,11 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t r_en
                     // the bulk copies overwrite it
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                     mbar_arrive_expect_tx(bar, vbytes + cbytes + zbytes);
-                    if (vbytes) bulk_copy_g2s(sval, A.val + va, vbytes, bar);
-                    if (cbytes) bulk_copy_g2s(scol, A.col + ca, cbytes, bar);
-                    if (zbytes) bulk_copy_g2s(buf, z + rb, 256u, bar);
+                    if (!skip_bulk) {
+                        if (vbytes) bulk_copy_g2s(sval, A.val + va, vbytes, bar);
+                        if (cbytes) bulk_copy_g2s(scol, A.col + ca, cbytes, bar);
+                        if (zbytes) bulk_copy_g2s(buf, z + rb, 256u, bar);
+                    }
                 }
                 // a z written earlier in the same kernel is copied by the lanes
                 // (generic proxy), so that the earlier writes are seen
@@ -212,7 +223,8 @@ __device__ __forceinline__ SpmvChunk spmv_prepare(const CSRView &A, int64_t r_en
 template <bool CHECKED, int CAP, bool L2X, class F>
 __device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int64_t r_end, int64_t warp,
                                           int64_t nwarps, const double *__restrict__ x,
-                                          const double *__restrict__ z, bool z_bulk, unsigned &err, F &&fn) {
+                                          const double *__restrict__ z, bool z_bulk, bool test_stall,
+                                          unsigned &err, F &&fn) {
     __shared__ __align__(8) unsigned long long s_bar[MAX_WARPS][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t step = nwarps * 32;
@@ -232,6 +244,8 @@ __device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int
     }
     __syncwarp();
     unsigned parity = 0u;  // bit k: phase of buffer k's barrier to wait for
+    const long long wait_limit = test_stall ? SPMV_TEST_WAIT_LIMIT : SPMV_WAIT_LIMIT;
+    const bool skip_bulk = test_stall;
     auto rowptrs = [&](int64_t r0, long long &b, long long &e) {
         const int64_t r = r0 + lane;
         b = 0;
@@ -243,21 +257,19 @@ __device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int
     };
     long long b0, e0, b1, e1, b2, e2;
     rowptrs(rb, b0, e0);
-    SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, rb, b0, e0, bufs, bars);
+    SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb, b0, e0, bufs, bars);
     rowptrs(rb + step, b1, e1);
     int cur = 0;
     for (; rb < r_end; rb += step) {
-        const SpmvChunk c1 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, rb + step, b1, e1,
-                                                       bufs + (cur ^ 1) * L::BUF, bars + (cur ^ 1));
+        const SpmvChunk c1 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb + step,
+                                                       b1, e1, bufs + (cur ^ 1) * L::BUF, bars + (cur ^ 1));
         rowptrs(rb + 2 * step, b2, e2);
         if (c0.how == CHUNK_BULK) {
             long long spins = 0;
-            while (!mbar_try_wait(bars + cur, (parity >> cur) & 1u)) {
-                if (++spins > SPMV_WAIT_LIMIT) {
-                    err |= ERR_TIMEOUT;
-                    break;
-                }
-            }
+            while (!mbar_try_wait(bars + cur, (parity >> cur) & 1u))
+                if (++spins > wait_limit) break;
+            // the whole warp leaves together if any lane's wait ran out
+            if (__any_sync(0xffffffffu, spins > wait_limit)) goto stalled;
             parity ^= 1u << cur;
         }
         __pipeline_wait_prior(1);  // chunk rb's per-lane copies have landed
@@ -318,14 +330,31 @@ __device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int
     // a bulk chunk prepared past the end is never waited for: there is none,
     // since prepare stages nothing for rb >= r_end
     __syncwarp();
+    return;
+stalled:
+    // A wait ran out (ERR_TIMEOUT): stage nothing more (a late copy could still
+    // land in the buffers) and read this and every later row from global memory.
+    err |= ERR_TIMEOUT;
+    for (; rb < r_end; rb += step) {
+        const int64_t r = rb + lane;
+        if (r < r_end) {
+            bool bad = false;
+            const double acc = spmv_row<L2X>(A, r, x, bad);
+            if (bad) err |= ERR_INDEX;
+            fn(r, acc, z ? z[r] : 0.0);
+        }
+    }
+    __pipeline_wait_prior(0);
+    __syncwarp();
 }
 
 // The whole matrix over the grid: every warp of every block.
 template <bool CHECKED, int CAP, class F>
 __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x,
-                                               const double *__restrict__ z, unsigned &err, F &&fn) {
+                                               const double *__restrict__ z, bool test_stall, unsigned &err,
+                                               F &&fn) {
     spmv_rows<CHECKED, CAP, false>(A, 0, A.n, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
-                                   (int64_t)gridDim.x * (blockDim.x >> 5), x, z, true, err, fn);
+                                   (int64_t)gridDim.x * (blockDim.x >> 5), x, z, true, test_stall, err, fn);
 }
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
@@ -337,8 +366,8 @@ __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * block
 template <bool CHECKED, int CAP, class F>
 __device__ __forceinline__ void spmv_each(const CSRView &A, const double *__restrict__ x,
                                           const double *__restrict__ z, int mode, unsigned &err, F &&fn) {
-    if (mode != 1) {
-        spmv_warp_rows<CHECKED, CAP>(A, x, z, err, fn);
+    if ((mode & SPMV_MODE_MASK) != 1) {
+        spmv_warp_rows<CHECKED, CAP>(A, x, z, (mode & SPMV_TEST_STALL) != 0, err, fn);
     } else {
         bool bad = false;
         for (int64_t i = gtid(); i < A.n; i += gstride()) fn(i, spmv_row(A, i, x, bad), z ? z[i] : 0.0);

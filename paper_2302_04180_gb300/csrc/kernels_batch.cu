@@ -174,7 +174,8 @@ template <class F>
 __device__ __forceinline__ void group_spmv(const SysView &V, const double *x, const double *z, bool &bad,
                                            F &&fn) {
     unsigned eb = 0u;
-    spmv_rows<true, SPMV_CAP_SHORT, true>(V.A, V.lo, V.hi, threadIdx.x >> 5, blockDim.x >> 5, x, z, false, eb, fn);
+    spmv_rows<true, SPMV_CAP_SHORT, true>(V.A, V.lo, V.hi, threadIdx.x >> 5, blockDim.x >> 5, x, z, false, false, eb,
+                                          fn);
     if (eb) bad = true;
 }
 

@@ -206,7 +206,7 @@ int spmv_blocks_per_sm(int block, int carveout, int mode) {
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s) {
     spmv_carveout(cfg.carveout);
-    const bool lng = cfg.mode == SPMV_MODE_LONG;
+    const bool lng = (cfg.mode & SPMV_MODE_MASK) == SPMV_MODE_LONG;
     if (st && lng) k_spmv<false, SPMV_CAP_LONG><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
     else if (st) k_spmv<false, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
     else if (lng) k_spmv<true, SPMV_CAP_LONG><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);

@@ -320,7 +320,7 @@ static cudaError_t setup_t(const SolverArgs &a, int variant, cudaStream_t s, Ker
         TIMED(PK_SETUP, (k_cls_setup<R1><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
     } else {
         TIMED(PK_SETUP, (k_pipe_setup1<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
-        if (a.spmv.mode == SPMV_MODE_LONG)
+        if ((a.spmv.mode & SPMV_MODE_MASK) == SPMV_MODE_LONG)
             TIMED(PK_SETUP, (k_pipe_setup2<R2, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         else
             TIMED(PK_SETUP, (k_pipe_setup2<R2, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
@@ -333,7 +333,7 @@ template <class R1, class R2, class R5>
 static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, KernelTimer *tm) {
     Ctx c = make_ctx(a);
     if (variant == RBS_CLASSIC) {
-        const bool lng = a.spmv.mode == SPMV_MODE_LONG;
+        const bool lng = (a.spmv.mode & SPMV_MODE_MASK) == SPMV_MODE_LONG;
         if (lng) TIMED(PK_SPMV_DOT, (k_cls_k1<R1, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         else TIMED(PK_SPMV_DOT, (k_cls_k1<R1, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k2<<<a.vec.grid, a.vec.block, 0, s>>>(c)));

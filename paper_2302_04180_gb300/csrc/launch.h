@@ -21,7 +21,9 @@ struct CSRArgs {
 
 // SpMV row schedules (Cfg::mode): one thread per row, warp-staged chunks of
 // up to SPMV_CAP_SHORT or SPMV_CAP_LONG nonzeros.
-enum : int { SPMV_MODE_ROW = 1, SPMV_MODE_SHORT = 2, SPMV_MODE_LONG = 3 };
+// Bit SPMV_TEST_STALL above the schedule bits selects the staged SpMV's test
+// mode of its bounded wait (kernels.cuh).
+enum : int { SPMV_MODE_ROW = 1, SPMV_MODE_SHORT = 2, SPMV_MODE_LONG = 3, SPMV_MODE_MASK = 0xff, SPMV_TEST_STALL = 0x100 };
 
 struct Cfg {
     int grid = 0;
