@@ -239,6 +239,43 @@ __device__ __forceinline__ void exact_add(Win<Q> &W, uint32_t &flags, unsigned l
     smem_deposit(sacc, u, L, m);
 }
 
+// The exact product x*y as five 32-bit words u (the 106-bit significand
+// product shifted left by pos & 31) at limb L = pos >> 5, sign mask m (0 or
+// ~0). Returns false, adding nothing, for a zero product; a non-finite operand
+// sets its flag and also returns false.
+__device__ __forceinline__ bool prod_exact(double x, double y, uint32_t &flags, uint32_t (&u)[5], int &L,
+                                           uint32_t &m) {
+    const uint32_t xh = (uint32_t)__double2hiint(x), xl = (uint32_t)__double2loint(x);
+    const uint32_t yh = (uint32_t)__double2hiint(y), yl = (uint32_t)__double2loint(y);
+    const uint32_t exm = xh & 0x7ff00000u, eym = yh & 0x7ff00000u;  // biased exponents << 20
+    uint32_t A1, B1;
+    int pos;
+    if (exm - 0x00100000u < 0x7fe00000u && eym - 0x00100000u < 0x7fe00000u) {
+        A1 = (xh & 0xfffffu) | 0x100000u;
+        B1 = (yh & 0xfffffu) | 0x100000u;
+        pos = (int)((exm >> 20) + (eym >> 20)) - 2;
+    } else {
+        const uint32_t ex = exm >> 20, ey = eym >> 20;
+        if (ex == 0x7ffu || ey == 0x7ffu) {
+            flags |= special_flags(xh, xl, yh, yl);
+            return false;
+        }
+        A1 = (xh & 0xfffffu) | (ex ? 0x100000u : 0u);
+        B1 = (yh & 0xfffffu) | (ey ? 0x100000u : 0u);
+        if ((A1 | xl) == 0u || (B1 | yl) == 0u) return false;
+        pos = (int)max(ex, 1u) + (int)max(ey, 1u) - 2;
+    }
+    const unsigned long long m00 = (unsigned long long)xl * yl;
+    const unsigned long long m01 = (unsigned long long)xl * B1 + (m00 >> 32);
+    const unsigned long long m10 = (unsigned long long)A1 * yl + (uint32_t)m01;
+    const unsigned long long m11 =
+        (unsigned long long)A1 * B1 + (unsigned long long)((uint32_t)(m01 >> 32) + (uint32_t)(m10 >> 32));
+    m = (uint32_t)((int32_t)(xh ^ yh) >> 31);
+    L = pos >> 5;
+    shift5((uint32_t)m00, (uint32_t)m10, (uint32_t)m11, (uint32_t)(m11 >> 32), (uint32_t)pos & 31u, u);
+    return true;
+}
+
 // Two windows per thread: H takes the product if it fits; a product above H
 // re-anchors H at it and the old H becomes the low window L; a product below H
 // goes to L (anchoring or re-anchoring it when it is empty or lies between L and
@@ -449,19 +486,20 @@ static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t 
     return __longlong_as_double((long long)bits);
 }
 
-// Grid-level finish of K exact reductions. Every thread of every block calls it
-// after its last exact_add. Returns true in the block that finishes last; there
-// the rounded values are in vals[0..K-1] (shared memory) after a barrier.
-template <int K, int Q, int SCRATCH = FLUSH_SCRATCH>
-__device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
-                                             unsigned long long (*sacc)[NL], uint32_t *sflags,
-                                             DotScratch *g, double *vals, bool export_limbs = false,
-                                             long long *limbs_out = nullptr, int32_t *flags_out = nullptr) {
+// Block- and grid-level finish of K exact reductions, once every thread's own
+// accumulators are in the block accumulators sacc (flags[k]: this thread's
+// non-finite flags). Every thread of every block calls it. Returns true in the
+// block that finishes last; there the rounded values are in vals[0..K-1]
+// (shared memory) after a barrier, or, with export_limbs, the partially
+// normalised limbs of the first reduction are in limbs_out.
+template <int K>
+__device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], unsigned long long (*sacc)[NL],
+                                                  uint32_t *sflags, DotScratch *g, double *vals,
+                                                  bool export_limbs = false, long long *limbs_out = nullptr,
+                                                  int32_t *flags_out = nullptr) {
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        warp_flush<Q, SCRATCH>(win[k], sacc[k]);
+    for (int k = 0; k < K; k++)
         if (flags[k]) atomicOr(&sflags[k], flags[k]);
-    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) {
         const int k = idx / NL, j = idx - k * NL;
@@ -493,6 +531,18 @@ __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)
     if (threadIdx.x < K) vals[threadIdx.x] = round_limbs_thread((long long *)sacc[threadIdx.x], sflags[threadIdx.x]);
     __syncthreads();
     return true;
+}
+
+// Grid-level finish of K exact reductions held in register windows: flush the
+// windows into the block accumulators, then block_grid_finish.
+template <int K, int Q, int SCRATCH = FLUSH_SCRATCH>
+__device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
+                                             unsigned long long (*sacc)[NL], uint32_t *sflags,
+                                             DotScratch *g, double *vals, bool export_limbs = false,
+                                             long long *limbs_out = nullptr, int32_t *flags_out = nullptr) {
+#pragma unroll
+    for (int k = 0; k < K; k++) warp_flush<Q, SCRATCH>(win[k], sacc[k]);
+    return block_grid_finish<K>(flags, sacc, sflags, g, vals, export_limbs, limbs_out, flags_out);
 }
 
 }  // namespace rbs

@@ -1,6 +1,7 @@
 // Standalone kernels: exact dot (single and multi-output), long-accumulator
 // export and rounding, fma-ordered SpMV, Jacobi, CSR validation.
 #include <mutex>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "launch.h"
@@ -15,10 +16,15 @@ struct DotArgs {
 
 // K exact dots over the same length (Sec. 2 exdot; Sec. 4.1/4.2 merged
 // reductions). Aligned operands go through 16-byte loads, two pairs deep.
+// One or two outputs keep their windows in shared memory (ExactS: fewer
+// integer operations per product), more in registers (ExactR2).
+template <int K, int Q>
+using ExdotRed = typename std::conditional<(K <= 2), ExactS<K>, ExactR2<K, Q>>::type;
+
 template <int K, int Q, bool EXPORT>
 __global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool aligned, DotScratch *g,
                                               double *out, long long *limbs, int32_t *flags_out) {
-    ExactR2<K, Q> red;
+    ExdotRed<K, Q> red;
     red.init();
     if (aligned) {
         const int64_t n2 = n >> 1, st = gstride();
@@ -61,8 +67,7 @@ __global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool ali
     }
     __shared__ double vals[K];
     if (EXPORT) {
-        red.flush_low();
-        exact_finish<K, Q>(red.win, red.flags, red.sacc, red.sflags, g, vals, true, limbs, flags_out);
+        red.finish_export(g, vals, limbs, flags_out);
     } else {
         if (red.finish(g, vals) && threadIdx.x < K) out[threadIdx.x] = vals[threadIdx.x];
     }

@@ -82,6 +82,122 @@ struct ExactR2 {
         flush_low<SCRATCH>();
         return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals);
     }
+    __device__ __forceinline__ bool finish_export(DotScratch *g, double *vals, long long *limbs, int32_t *fl) {
+        flush_low();
+        return exact_finish<K, Q>(win, flags, sacc, sflags, g, vals, true, limbs, fl);
+    }
+};
+
+// Exact reducer for standalone dots of one or two outputs, with the
+// per-thread window in shared memory instead of registers: 64-bit carry-save
+// digits, W per sign (positive and negative products kept apart, so a product
+// adds its five words to five digits picked by address -- no word selects, no
+// two's complement). Layout [K][sign][digit][thread], so the lanes of a warp
+// touch consecutive words. The window covers W - 4 = 9 placements (288 bits
+// of exponent); the product that anchors it lands at placement ANCHOR, with
+// 3 placements of headroom above and 5 below (measured best across condition
+// numbers 1 to 1e48). A product above it flushes and re-anchors it, one below
+// it goes straight into the block accumulator. Digits stay below 2^52 (at most
+// 2^20 products per thread per launch, 2^32 each). Blocks of at most 256
+// threads.
+template <int K_>
+struct ExactS {
+    static constexpr int K = K_;
+    static constexpr int W = 13;
+    static constexpr int ANCHOR = 5;  // placement of the product that (re)anchors the window
+    static constexpr int NT = 256;
+    long long *win;
+    int a[K];
+    uint32_t flags[K];
+    unsigned long long (*sacc)[NL];
+    uint32_t *sflags;
+
+    __device__ __forceinline__ void init() {
+        __shared__ long long s_win[K * 2 * W * NT];
+        __shared__ unsigned long long s_acc[K][NL];
+        __shared__ uint32_t s_flags[K];
+        win = s_win;
+        sacc = s_acc;
+        sflags = s_flags;
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            a[k] = WIN_EMPTY;
+            flags[k] = 0u;
+#pragma unroll
+            for (int j = 0; j < 2 * W; j++) win[(k * 2 * W + j) * NT + threadIdx.x] = 0;
+        }
+        sacc_zero<K>(sacc, sflags);
+    }
+    // this thread's window k into the block accumulator, digits back to zero
+    __device__ __forceinline__ void flush(int k) {
+        if (a[k] < 0) return;
+        long long *pp = win + (k * 2 * W) * NT + threadIdx.x, *pn = pp + W * NT;
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            const long long d = pp[j * NT] - pn[j * NT];
+            pp[j * NT] = 0;
+            pn[j * NT] = 0;
+            if (d) atomicAdd(&sacc[k][a[k] + j], (unsigned long long)d);
+        }
+    }
+    __device__ __forceinline__ void add(int k, double x, double y) {
+        uint32_t u[5], m;
+        int L;
+        if (!prod_exact(x, y, flags[k], u, L, m)) return;
+        int q = L - a[k];
+        if ((unsigned)q > (unsigned)(W - 5)) {
+            if (q < 0) {  // below the window (never for an empty one: its anchor is far below)
+                smem_deposit(sacc[k], u, L, m);
+                return;
+            }
+            flush(k);
+            a[k] = L - ANCHOR < 0 ? 0 : L - ANCHOR;
+            q = L - a[k];
+        }
+        long long *p = win + ((k * 2 + (int)(m & 1u)) * W + q) * NT + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < 5; j++) p[j * NT] += (long long)u[j];
+    }
+    // Warp-cooperative flush of every lane's window k (all 32 lanes call it):
+    // the lanes' windows usually sit on the same limbs, so per-lane atomics
+    // would collide 32 ways; instead lane j sums every lane's digit of limb
+    // lo + j straight from shared memory and adds it with one atomic.
+    // Windows spread over more than 32 limbs fall back to per-lane flushes.
+    __device__ __forceinline__ void flush_warp(int k) {
+        const unsigned FULL = 0xffffffffu;
+        const int lane = threadIdx.x & 31;
+        const bool has = a[k] >= 0;
+        const int lo = (int)__reduce_min_sync(FULL, (unsigned)(has ? a[k] : 0x7fffffff));
+        const int hi = (int)__reduce_max_sync(FULL, (unsigned)(has ? a[k] : 0));
+        if (lo == 0x7fffffff) return;
+        if (hi - lo > 32 - W) {
+            flush(k);
+            return;
+        }
+        const long long *w0 = win + (k * 2 * W) * NT + (threadIdx.x & ~31);
+        long long sum = 0;
+        for (int l = 0; l < 32; l++) {
+            const int al = __shfl_sync(FULL, a[k], l);
+            const int j = lo + lane - al;
+            if (al >= 0 && j >= 0 && j < W) sum += w0[j * NT + l] - w0[(W + j) * NT + l];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 2 * W; j++) win[(k * 2 * W + j) * NT + threadIdx.x] = 0;
+        if (sum && lo + lane < NL) atomicAdd(&sacc[k][lo + lane], (unsigned long long)sum);
+        a[k] = WIN_EMPTY;
+    }
+    template <int SCRATCH = 0>
+    __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
+#pragma unroll
+        for (int k = 0; k < K; k++) flush_warp(k);
+        return block_grid_finish<K>(flags, sacc, sflags, g, vals);
+    }
+    __device__ __forceinline__ bool finish_export(DotScratch *g, double *vals, long long *limbs, int32_t *fl) {
+#pragma unroll
+        for (int k = 0; k < K; k++) flush_warp(k);
+        return block_grid_finish<K>(flags, sacc, sflags, g, vals, true, limbs, fl);
+    }
 };
 
 template <int K_>
