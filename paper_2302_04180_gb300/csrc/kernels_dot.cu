@@ -16,15 +16,17 @@ struct DotArgs {
 
 // K exact dots over the same length (Sec. 2 exdot; Sec. 4.1/4.2 merged
 // reductions). Aligned operands go through 16-byte loads, two pairs deep.
-// One or two outputs keep their windows in shared memory (ExactS: fewer
-// integer operations per product), more in registers (ExactR2).
-template <int K, int Q>
-using ExdotRed = typename std::conditional<(K <= 2), ExactS<K>, ExactR2<K, Q>>::type;
+// SMEM: one or two outputs keep their windows in shared memory (ExactS: fewer
+// integer operations per product, dearer to clear and flush per thread); long
+// dots take it, short ones and more outputs keep register windows (ExactR2).
+template <int K, int Q, bool SMEM>
+using ExdotRed = typename std::conditional<(SMEM && K <= 2), ExactS<K>, ExactR2<K, Q>>::type;
+constexpr int64_t EXDOT_SMEM_MIN_N = 1LL << 23;  // measured crossover on GB300
 
-template <int K, int Q, bool EXPORT>
+template <int K, int Q, bool EXPORT, bool SMEM>
 __global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool aligned, DotScratch *g,
                                               double *out, long long *limbs, int32_t *flags_out) {
-    ExdotRed<K, Q> red;
+    ExdotRed<K, Q, SMEM> red;
     red.init();
     if (aligned) {
         const int64_t n2 = n >> 1, st = gstride();
@@ -83,7 +85,10 @@ static cudaError_t exdot_k(const double *const *xs, const double *const *ys, int
         a.y[k] = ys[k];
         aligned = aligned && ((uintptr_t)xs[k] % 16 == 0) && ((uintptr_t)ys[k] % 16 == 0);
     }
-    k_exdot<K, Q, false><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, out, nullptr, nullptr);
+    if (K <= 2 && n >= EXDOT_SMEM_MIN_N)
+        k_exdot<K, Q, false, true><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, out, nullptr, nullptr);
+    else
+        k_exdot<K, Q, false, false><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, out, nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -101,17 +106,17 @@ static cudaError_t exdot_q(int k, const double *const *xs, const double *const *
     }
 }
 
-template <int Q>
+template <int Q, bool SMEM>
 static int exdot_occ_q(int k, int block) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (k) {
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<1, Q, false>, block, 0); break;
-        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<2, Q, false>, block, 0); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<3, Q, false>, block, 0); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<4, Q, false>, block, 0); break;
-        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<5, Q, false>, block, 0); break;
-        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<6, Q, false>, block, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<1, Q, false, SMEM>, block, 0); break;
+        case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<2, Q, false, SMEM>, block, 0); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<3, Q, false, false>, block, 0); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<4, Q, false, false>, block, 0); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<5, Q, false, false>, block, 0); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_exdot<6, Q, false, false>, block, 0); break;
         default: break;
     }
     if (e != cudaSuccess || nb < 1) {
@@ -121,10 +126,11 @@ static int exdot_occ_q(int k, int block) {
     return nb;
 }
 
-int exdot_blocks_per_sm(int k, int window, int block) {
-    if (window == 2) return exdot_occ_q<2>(k, block);
-    if (window == 1) return exdot_occ_q<1>(k, block);
-    return exdot_occ_q<4>(k, block);
+int exdot_blocks_per_sm(int k, int window, int block, int64_t n) {
+    const bool smem = k <= 2 && n >= EXDOT_SMEM_MIN_N;
+    if (window == 2) return smem ? exdot_occ_q<2, true>(k, block) : exdot_occ_q<2, false>(k, block);
+    if (window == 1) return smem ? exdot_occ_q<1, true>(k, block) : exdot_occ_q<1, false>(k, block);
+    return smem ? exdot_occ_q<4, true>(k, block) : exdot_occ_q<4, false>(k, block);
 }
 
 cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,
@@ -141,8 +147,12 @@ cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, Do
     a.x[0] = x;
     a.y[0] = y;
     const bool aligned = ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0);
-    k_exdot<1, 4, true><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, nullptr, (long long *)limbs,
-                                                        flags);
+    if (n >= EXDOT_SMEM_MIN_N)
+        k_exdot<1, 4, true, true><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, nullptr, (long long *)limbs,
+                                                              flags);
+    else
+        k_exdot<1, 4, true, false><<<cfg.grid, cfg.block, 0, s>>>(a, n, aligned, g, nullptr, (long long *)limbs,
+                                                               flags);
     return cudaGetLastError();
 }
 

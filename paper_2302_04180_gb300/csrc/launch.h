@@ -45,8 +45,9 @@ cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, Do
 cudaError_t launch_fpe_dot(const double *x, const double *y, int64_t n, DotScratch *g, double *out,
                            unsigned *lost, Cfg cfg, cudaStream_t s);
 // Resident blocks per SM of the k-output exact-dot kernel (window Q) at this
-// block size: the persistent grid is a whole number of waves of it.
-int exdot_blocks_per_sm(int k, int window, int block);
+// block size, for dots of length n (the kernel variant depends on it): the
+// persistent grid is a whole number of waves of it.
+int exdot_blocks_per_sm(int k, int window, int block, int64_t n);
 int fpe_blocks_per_sm(int block);
 cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, cudaStream_t s);
 // y = A x. Without a solver state every index is checked (ERR_INDEX on a bad

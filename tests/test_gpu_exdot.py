@@ -191,3 +191,22 @@ def test_nonfinite_inside_long_vectors(rbs, dev, orc):
         xx, yy = x.copy(), y.copy()
         xx[pos], yy[pos] = xv, yv
         assert same(_gpu(rbs, dev, xx, yy), orc.exdot(xx, yy))
+
+
+def test_long_dots_take_the_shared_window_path(rbs, dev, orc):
+    """Dots of at least 2^23 elements keep one or two outputs' windows in
+    shared memory: single, two-output and limb-export results against the
+    oracle, with a ragged tail, a wide exponent spread and non-finite values."""
+    import torch
+    n = (1 << 23) + 3
+    x, y, exact = gen.ill_conditioned_dot(n, 1e40, 11)
+    w = gen.random_vector(n, 12, 3) * 10.0 ** gen.random_vector(n, 12, 4, -150, 150)
+    xt, yt, wt = (torch.from_numpy(v).to(dev) for v in (x, y, w))
+    assert same(rbs.rbs_exdot(xt, yt).item(), float(exact))
+    two = rbs.rbs_exdot_multi([xt, wt], [yt, wt]).cpu().numpy()
+    assert same(two[0], float(exact)) and same(two[1], orc.exdot(w, w))
+    limbs, flags = rbs.rbs_exdot_partial(wt, yt)
+    assert same(rbs.rbs_round_limbs(limbs, flags).item(), orc.exdot(w, y))
+    ww = w.copy()
+    ww[n // 2] = np.inf
+    assert same(rbs.rbs_exdot(torch.from_numpy(ww).to(dev), yt).item(), orc.exdot(ww, y))
