@@ -207,8 +207,10 @@ typedef struct {
 typedef struct {
     int64_t launches[RBS_PROF_KINDS];
     double ms[RBS_PROF_KINDS];
-    /* kinds: 0 SpMV (+dot epilogue), 1 vector update (+dots), 2 set-up,
-       3 standalone SpMV (pipelined S10/S18), 4..7 unused */
+    /* kinds: 0 SpMV with a dot epilogue (classic K1, K3), 1 vector update
+       without dots (classic K2, K5), 2 set-up, 3 standalone SpMV (pipelined
+       S10/S18), 4 vector update with dots (classic K4, pipelined P1, P3),
+       5..7 unused */
 } rbs_prof;
 
 /* Solve A x = b with Jacobi-preconditioned BiCGStab (Fig. 2) or pipelined

@@ -30,7 +30,7 @@ RBS_LIMBS = 136
 RBS_NOALLOC_MAX_DOTS = 6
 RBS_HIST_W = 12
 RBS_PROF_KINDS = 8
-PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv")
+PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv", "vec_dot")
 
 # every symbol include/rbs.h declares
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",

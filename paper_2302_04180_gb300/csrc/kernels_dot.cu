@@ -393,7 +393,7 @@ extern "C" int rbs_exdot_noalloc(int k, const double *const *xs, const double *c
     Cfg c;
     c.block = 256;
     int64_t g = (n + 2LL * c.block - 1) / (2LL * c.block);
-    const int64_t cap = (int64_t)sms * 4;
+    const int64_t cap = (int64_t)sms * exdot_blocks_per_sm(k, 4, c.block, n);  // whole waves
     g = g < 1 ? 1 : (g < cap ? g : cap);
     const int64_t minimum = (n + ((int64_t)c.block << 20) - 1) / ((int64_t)c.block << 20);
     if (g < minimum) g = minimum;

@@ -339,12 +339,12 @@ static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, Kern
         TIMED(PK_VEC, (k_cls_k2<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         if (lng) TIMED(PK_SPMV_DOT, (k_cls_k3<R2, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         else TIMED(PK_SPMV_DOT, (k_cls_k3<R2, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
-        TIMED(PK_VEC, (k_cls_k4<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_VEC_DOT, (k_cls_k4<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k5<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
     } else {
-        TIMED(PK_VEC, (k_pipe_p1<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_VEC_DOT, (k_pipe_p1<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         TIMED(PK_SPMV, (launch_spmv(a.A, a.v.zh, a.v.v, a.st, a.err, a.spmv, s)));
-        TIMED(PK_VEC, (k_pipe_p3<R5><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_VEC_DOT, (k_pipe_p3<R5><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         TIMED(PK_SPMV, (launch_spmv(a.A, a.v.wh, a.v.t, a.st, a.err, a.spmv, s)));
     }
     return cudaGetLastError();

@@ -81,7 +81,7 @@ struct SolverArgs {
 };
 
 // Kernel kinds for profiling (rbs_prof.kinds).
-enum ProfKind { PK_SPMV_DOT = 0, PK_VEC = 1, PK_SETUP = 2, PK_SPMV = 3 };
+enum ProfKind { PK_SPMV_DOT = 0, PK_VEC = 1, PK_SETUP = 2, PK_SPMV = 3, PK_VEC_DOT = 4 };
 
 struct KernelTimer {
     virtual void before(int kind) = 0;
