@@ -263,10 +263,14 @@ int window_param() {
     return (q == 1 || q == 2 || q == 4) ? (int)q : 4;
 }
 
+// Per-kernel CUDA events. Kernels enqueued back to back share events: a
+// kernel's start is the previous kernel's end, so each launch records one
+// event; gap() marks other work in between (the next start is recorded anew).
 struct EventTimer : KernelTimer {
     Workspace *w;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> rec;
     size_t used = 0;
+    cudaEvent_t last_end = nullptr;
     cudaError_t err = cudaSuccess;
     explicit EventTimer(Workspace *ws) : w(ws) {}
     cudaEvent_t take() {
@@ -282,18 +286,24 @@ struct EventTimer : KernelTimer {
         return w->evpool[used++];
     }
     void before(int kind) override {
-        cudaEvent_t a = take();
-        if (!a) return;
-        cudaEventRecord(a, w->stream);
+        cudaEvent_t a = last_end;
+        if (!a) {
+            a = take();
+            if (!a) return;
+            cudaEventRecord(a, w->stream);
+        }
         rec.push_back({kind, {a, nullptr}});
     }
     void after(int kind) override {
         (void)kind;
         cudaEvent_t b = take();
+        last_end = nullptr;
         if (!b || rec.empty()) return;
         cudaEventRecord(b, w->stream);
         rec.back().second.second = b;
+        last_end = b;
     }
+    void gap() override { last_end = nullptr; }
 };
 
 // Build (or reuse) the executable graph whose WHILE node replays one solver
@@ -674,6 +684,7 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
             CK(cudaMemcpyAsync(&w->h_flags[cur], &w->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                w->stream));
             CK(cudaEventRecord(w->ev_chunk[cur], w->stream));
+            if (tm) tm->gap();
             slot ^= 1;
         }
         if (prev >= 0) {

@@ -86,6 +86,7 @@ enum ProfKind { PK_SPMV_DOT = 0, PK_VEC = 1, PK_SETUP = 2, PK_SPMV = 3, PK_VEC_D
 struct KernelTimer {
     virtual void before(int kind) = 0;
     virtual void after(int kind) = 0;
+    virtual void gap() {}  // other work was enqueued since the last after()
     virtual ~KernelTimer() {}
 };
 
