@@ -150,7 +150,7 @@ def run_reference(args):
             "data": "synthetic", "config": _workload_config(A),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"per step: set-up + {per} classic iteration of the "
-                                       "256^3 solve, single-threaded C oracle"},
+                                       f"{GRID}^3 solve, single-threaded C oracle"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
