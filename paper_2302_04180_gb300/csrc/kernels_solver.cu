@@ -230,8 +230,10 @@ __global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
     const double al = c.st->alpha, nal = -al, be = c.st->beta, nom = -c.st->omega;
     const bool first = c.st->iter == 0;
     for (int64_t i = gtid(); i < c.n; i += gstride()) {
+        // Every operand is loaded before the first store so that the loads of one
+        // element overlap (the vectors are not declared restrict).
         double ph, s, sh, z;
-        const double rh = c.rh[i], w = c.w[i], wh = c.wh[i], t = c.t[i];
+        const double rh = c.rh[i], w = c.w[i], wh = c.wh[i], t = c.t[i], r = c.r[i], d = c.invd[i];
         if (first) {
             ph = rh;
             s = w;
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
             sh = fma(be, fma(nom, zh0, sh0), wh);
             z = fma(be, fma(nom, v0, z0), t);
         }
-        const double q = fma(nal, s, c.r[i]);
+        const double q = fma(nal, s, r);
         const double qh = fma(nal, sh, rh);
         const double y = fma(nal, z, w);
         c.ph[i] = ph;
@@ -255,7 +257,7 @@ __global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
         c.q[i] = q;
         c.qh[i] = qh;
         c.y[i] = y;
-        c.zh[i] = __dmul_rn(z, c.invd[i]);
+        c.zh[i] = __dmul_rn(z, d);
         red.add(0, q, y);
         red.add_sq(1, y);
     }
@@ -263,29 +265,35 @@ __global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_omega(c.st, vals);
 }
 
+template <class R> struct P3Blocks { static constexpr int value = 4; };
+template <int K> struct P3Blocks<PlainR<K>> { static constexpr int value = 3; };
+
 // P3: S12-S15, S17; <r0,r>, <r0,w>, <r0,s>, <r0,z>, <r,r> -> tau, beta, alpha.
-// Four blocks per SM (64 registers, a few spilled) measured faster than three.
+// With the exact reducer four blocks per SM (64 registers, some spilled) measured
+// faster than three; with the plain one three measured faster than four.
 template <class R>
-__global__ void __launch_bounds__(256, 4) k_pipe_p3(Ctx c) {
+__global__ void __launch_bounds__(256, P3Blocks<R>::value) k_pipe_p3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     const double al = c.st->alpha, nal = -al, om = c.st->omega, nom = -om;
     for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        const double qh = c.qh[i], y = c.y[i], q = c.q[i];
-        c.x[i] = fma(om, qh, fma(al, c.ph[i], c.x[i]));
+        // Every operand is loaded before the first store (see P1).
+        const double qh = c.qh[i], y = c.y[i], q = c.q[i], ph = c.ph[i], x0 = c.x[i], zh = c.zh[i],
+                     wh0 = c.wh[i], v = c.v[i], t = c.t[i], d = c.invd[i], r0 = c.r0[i], s = c.s[i],
+                     z = c.z[i];
+        c.x[i] = fma(om, qh, fma(al, ph, x0));
         const double r = fma(nom, y, q);
-        const double rh = fma(nom, fma(nal, c.zh[i], c.wh[i]), qh);
-        const double w = fma(nom, fma(nal, c.v[i], c.t[i]), y);
+        const double rh = fma(nom, fma(nal, zh, wh0), qh);
+        const double w = fma(nom, fma(nal, v, t), y);
         c.r[i] = r;
         c.rh[i] = rh;
         c.w[i] = w;
-        c.wh[i] = __dmul_rn(w, c.invd[i]);
-        const double r0 = c.r0[i];
+        c.wh[i] = __dmul_rn(w, d);
         red.add(0, r0, r);
         red.add(1, r0, w);
-        red.add(2, r0, c.s[i]);
-        red.add(3, r0, c.z[i]);
+        red.add(2, r0, s);
+        red.add(3, r0, z);
         red.add_sq(4, r);
     }
     __shared__ double vals[R::K];
