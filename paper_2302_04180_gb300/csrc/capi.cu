@@ -634,7 +634,11 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         const int smode = spmv_mode_for(n, nnz);
         const int bps = solver_blocks_per_sm(variant, o.dot_mode, 1, vb, carve, smode & SPMV_MODE_MASK);
         a.vec = grid_for(w, (n + 1) / 2, vb, bps);
-        if (p_vec_grid.load() > 0) a.vec.grid = (int)p_vec_grid.load();
+        a.p3 = variant == RBS_PIPELINED
+                   ? grid_for(w, (n + 1) / 2, vb, solver_blocks_per_sm(variant, o.dot_mode, 2, vb, carve,
+                                                                       smode & SPMV_MODE_MASK))
+                   : a.vec;
+        if (p_vec_grid.load() > 0) a.vec.grid = a.p3.grid = (int)p_vec_grid.load();
         const int sb = block_of(p_spmv_block.load(), 256);
         a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve, smode & SPMV_MODE_MASK));
         a.spmv.mode = smode;
@@ -643,6 +647,7 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         // window headroom: at most 2^20 products per thread per launch
         const int64_t minv = (n + ((int64_t)a.vec.block << 20) - 1) / ((int64_t)a.vec.block << 20);
         if (a.vec.grid < minv) a.vec.grid = (int)minv;
+        if (a.p3.grid < minv) a.p3.grid = (int)minv;
         const int64_t mins = (n + ((int64_t)a.spmv.block << 20) - 1) / ((int64_t)a.spmv.block << 20);
         if (a.spmv.grid < mins) a.spmv.grid = (int)mins;
     }

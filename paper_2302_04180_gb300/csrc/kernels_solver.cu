@@ -265,36 +265,80 @@ __global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_omega(c.st, vals);
 }
 
-template <class R> struct P3Blocks { static constexpr int value = 4; };
-template <int K> struct P3Blocks<PlainR<K>> { static constexpr int value = 3; };
+template <class R> struct P3Cfg { static constexpr int blocks = 2, pairs = 1; };
+template <int K> struct P3Cfg<PlainR<K>> { static constexpr int blocks = 3, pairs = 0; };
+
+// P3 for one element, from its thirteen operands (loaded by the caller before
+// any store): x, r, rhat, w and what, and the five dots' products.
+struct P3In {
+    double qh, y, q, ph, x, zh, wh, v, t, d, r0, s, z;
+};
+struct P3Out {
+    double x, r, rh, w, wh;
+};
+template <class R>
+__device__ __forceinline__ P3Out p3_elem(const P3In &a, double al, double nal, double om, double nom, R &red) {
+    P3Out o;
+    o.x = fma(om, a.qh, fma(al, a.ph, a.x));
+    o.r = fma(nom, a.y, a.q);
+    o.rh = fma(nom, fma(nal, a.zh, a.wh), a.qh);
+    o.w = fma(nom, fma(nal, a.v, a.t), a.y);
+    o.wh = __dmul_rn(o.w, a.d);
+    red.add(0, a.r0, o.r);
+    red.add(1, a.r0, o.w);
+    red.add(2, a.r0, a.s);
+    red.add(3, a.r0, a.z);
+    red.add_sq(4, o.r);
+    return o;
+}
 
 // P3: S12-S15, S17; <r0,r>, <r0,w>, <r0,s>, <r0,z>, <r,r> -> tau, beta, alpha.
-// With the exact reducer four blocks per SM (64 registers, some spilled) measured
-// faster than three; with the plain one three measured faster than four.
+// Every operand of an element is loaded before its first store (the vectors are
+// not restrict-qualified, so later loads could not be issued early).
 template <class R>
-__global__ void __launch_bounds__(256, P3Blocks<R>::value) k_pipe_p3(Ctx c) {
+__global__ void __launch_bounds__(256, P3Cfg<R>::blocks) k_pipe_p3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     const double al = c.st->alpha, nal = -al, om = c.st->omega, nom = -om;
-    for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        // Every operand is loaded before the first store (see P1).
-        const double qh = c.qh[i], y = c.y[i], q = c.q[i], ph = c.ph[i], x0 = c.x[i], zh = c.zh[i],
-                     wh0 = c.wh[i], v = c.v[i], t = c.t[i], d = c.invd[i], r0 = c.r0[i], s = c.s[i],
-                     z = c.z[i];
-        c.x[i] = fma(om, qh, fma(al, ph, x0));
-        const double r = fma(nom, y, q);
-        const double rh = fma(nom, fma(nal, zh, wh0), qh);
-        const double w = fma(nom, fma(nal, v, t), y);
-        c.r[i] = r;
-        c.rh[i] = rh;
-        c.w[i] = w;
-        c.wh[i] = __dmul_rn(w, d);
-        red.add(0, r0, r);
-        red.add(1, r0, w);
-        red.add(2, r0, s);
-        red.add(3, r0, z);
-        red.add_sq(4, r);
+    if (P3Cfg<R>::pairs) {
+        for_pairs(c.n, [&](int64_t i, bool pair) {
+            if (pair) {
+                const double2 qh = ld2(c.qh, i), y = ld2(c.y, i), q = ld2(c.q, i), ph = ld2(c.ph, i),
+                              x = ld2(c.x, i), zh = ld2(c.zh, i), wh = ld2(c.wh, i), v = ld2(c.v, i),
+                              t = ld2(c.t, i), d = ld2(c.invd, i), r0 = ld2(c.r0, i), s = ld2(c.s, i),
+                              z = ld2(c.z, i);
+                const P3Out o0 = p3_elem(P3In{qh.x, y.x, q.x, ph.x, x.x, zh.x, wh.x, v.x, t.x, d.x, r0.x, s.x, z.x},
+                                         al, nal, om, nom, red);
+                const P3Out o1 = p3_elem(P3In{qh.y, y.y, q.y, ph.y, x.y, zh.y, wh.y, v.y, t.y, d.y, r0.y, s.y, z.y},
+                                         al, nal, om, nom, red);
+                st2(c.x, i, make_double2(o0.x, o1.x));
+                st2(c.r, i, make_double2(o0.r, o1.r));
+                st2(c.rh, i, make_double2(o0.rh, o1.rh));
+                st2(c.w, i, make_double2(o0.w, o1.w));
+                st2(c.wh, i, make_double2(o0.wh, o1.wh));
+            } else {
+                const P3Out o = p3_elem(P3In{c.qh[i], c.y[i], c.q[i], c.ph[i], c.x[i], c.zh[i], c.wh[i], c.v[i],
+                                             c.t[i], c.invd[i], c.r0[i], c.s[i], c.z[i]},
+                                        al, nal, om, nom, red);
+                c.x[i] = o.x;
+                c.r[i] = o.r;
+                c.rh[i] = o.rh;
+                c.w[i] = o.w;
+                c.wh[i] = o.wh;
+            }
+        });
+    } else {
+        for (int64_t i = gtid(); i < c.n; i += gstride()) {
+            const P3Out o = p3_elem(P3In{c.qh[i], c.y[i], c.q[i], c.ph[i], c.x[i], c.zh[i], c.wh[i], c.v[i], c.t[i],
+                                         c.invd[i], c.r0[i], c.s[i], c.z[i]},
+                                    al, nal, om, nom, red);
+            c.x[i] = o.x;
+            c.r[i] = o.r;
+            c.rh[i] = o.rh;
+            c.w[i] = o.w;
+            c.wh[i] = o.wh;
+        }
     }
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_beta(c.st, vals, c.hist);
@@ -353,7 +397,7 @@ static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, Kern
     } else {
         TIMED(PK_VEC_DOT, (k_pipe_p1<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         TIMED(PK_SPMV, (launch_spmv(a.A, a.v.zh, a.v.v, a.st, a.err, a.spmv, s)));
-        TIMED(PK_VEC_DOT, (k_pipe_p3<R5><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        TIMED(PK_VEC_DOT, (k_pipe_p3<R5><<<a.p3.grid, a.p3.block, 0, s>>>(c)));
         TIMED(PK_SPMV, (launch_spmv(a.A, a.v.wh, a.v.t, a.st, a.err, a.spmv, s)));
     }
     return cudaGetLastError();
@@ -438,7 +482,8 @@ int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int ca
                                                                         0);
             nb = nb2 < nb ? nb2 : nb;
         } else if (variant == RBS_PIPELINED) {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, block, 0);
+            e = which == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, block, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p1<PlainR<2>>, block, 0);
         } else {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<PlainR<2>>, block, 0);
         }
@@ -451,7 +496,8 @@ int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int ca
                                                                     0);
         nb = nb2 < nb ? nb2 : nb;
     } else if (variant == RBS_PIPELINED) {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, block, 0);
+        e = which == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, block, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p1<ExactR<2, SQ>>, block, 0);
     } else {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<ExactR<2, SQ>>, block, 0);
     }

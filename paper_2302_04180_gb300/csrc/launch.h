@@ -78,6 +78,7 @@ struct SolverArgs {
     int dot_mode;
     int carveout;  // shared-memory carveout percent for staging kernels, -1 = driver default
     Cfg vec, spmv;
+    Cfg p3;  // the pipelined P3 kernel, sized from its own occupancy
 };
 
 // Kernel kinds for profiling (rbs_prof.kinds).
@@ -127,7 +128,8 @@ cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, const in
 // Clusters of `csize` CTAs that fit on the device at once (0 if none).
 int batch_max_clusters(int csize);
 
-// occupancy-derived persistent grid for the kernels of one kind
+// occupancy-derived persistent grid for the kernels of one kind: which = 0 the
+// SpMV kernels, 1 the vector kernels, 2 the pipelined P3 kernel
 int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout, int spmv_mode);
 // Resident blocks per SM of the standalone SpMV kernel at this block size and
 // shared-memory carveout (applies the carveout first).
