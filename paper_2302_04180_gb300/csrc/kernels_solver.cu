@@ -221,50 +221,119 @@ __global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_pipe_setu
     if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
 }
 
-// P1: S1-S4 (copies at iteration 0), S5-S7, S9; <q,y>, <y,y> -> omega
+// Launch shape of P1 and P3 per reducer (blocks per SM; two elements per thread
+// with 16-byte accesses or one), the fastest measured on Poisson 256^3. With the
+// exact reducer, pairs issue twice the loads per thread and lower occupancy
+// keeps the dot windows in registers: P3 at two blocks uses 121 registers, no
+// spills, where four blocks spilled the five windows; P1 is best at three.
+template <class R> struct P1Cfg { static constexpr int blocks = 3, pairs = 1; };
+template <int K> struct P1Cfg<PlainR<K>> { static constexpr int blocks = 4, pairs = 0; };
+
+// P1 for one element: in[0..5] = rh, w, wh, t, r, invd and, after iteration 0,
+// in[6..11] = ph, s, sh, z, zh, v (all loaded by the caller before any store);
+// out = ph, s, sh, z, q, qh, y, zh.
+struct P1In {
+    double rh, w, wh, t, r, d, ph, s, sh, z, zh, v;
+};
+struct P1Out {
+    double ph, s, sh, z, q, qh, y, zh;
+};
 template <class R>
-__global__ void __launch_bounds__(256) k_pipe_p1(Ctx c) {
+__device__ __forceinline__ P1Out p1_elem(const P1In &a, bool first, double nal, double be, double nom, R &red) {
+    P1Out o;
+    if (first) {
+        o.ph = a.rh;
+        o.s = a.w;
+        o.sh = a.wh;
+        o.z = a.t;
+    } else {
+        o.ph = fma(be, fma(nom, a.sh, a.ph), a.rh);
+        o.s = fma(be, fma(nom, a.z, a.s), a.w);
+        o.sh = fma(be, fma(nom, a.zh, a.sh), a.wh);
+        o.z = fma(be, fma(nom, a.v, a.z), a.t);
+    }
+    o.q = fma(nal, o.s, a.r);
+    o.qh = fma(nal, o.sh, a.rh);
+    o.y = fma(nal, o.z, a.w);
+    o.zh = __dmul_rn(o.z, a.d);
+    red.add(0, o.q, o.y);
+    red.add_sq(1, o.y);
+    return o;
+}
+
+__device__ __forceinline__ P1In p1_load(const Ctx &c, int64_t i, bool first) {
+    P1In a{c.rh[i], c.w[i], c.wh[i], c.t[i], c.r[i], c.invd[i], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (!first) {
+        a.ph = c.ph[i];
+        a.s = c.s[i];
+        a.sh = c.sh[i];
+        a.z = c.z[i];
+        a.zh = c.zh[i];
+        a.v = c.v[i];
+    }
+    return a;
+}
+
+__device__ __forceinline__ void p1_store(const Ctx &c, int64_t i, const P1Out &o) {
+    c.ph[i] = o.ph;
+    c.s[i] = o.s;
+    c.sh[i] = o.sh;
+    c.z[i] = o.z;
+    c.q[i] = o.q;
+    c.qh[i] = o.qh;
+    c.y[i] = o.y;
+    c.zh[i] = o.zh;
+}
+
+// P1: S1-S4 (copies at iteration 0), S5-S7, S9; <q,y>, <y,y> -> omega.
+// Every operand of an element is loaded before its first store (the vectors are
+// not restrict-qualified, so later loads could not be issued early).
+template <class R>
+__global__ void __launch_bounds__(256, P1Cfg<R>::blocks) k_pipe_p1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     const double al = c.st->alpha, nal = -al, be = c.st->beta, nom = -c.st->omega;
     const bool first = c.st->iter == 0;
-    for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        // Every operand is loaded before the first store so that the loads of one
-        // element overlap (the vectors are not declared restrict).
-        double ph, s, sh, z;
-        const double rh = c.rh[i], w = c.w[i], wh = c.wh[i], t = c.t[i], r = c.r[i], d = c.invd[i];
-        if (first) {
-            ph = rh;
-            s = w;
-            sh = wh;
-            z = t;
-        } else {
-            const double ph0 = c.ph[i], s0 = c.s[i], sh0 = c.sh[i], z0 = c.z[i], zh0 = c.zh[i],
-                         v0 = c.v[i];
-            ph = fma(be, fma(nom, sh0, ph0), rh);
-            s = fma(be, fma(nom, z0, s0), w);
-            sh = fma(be, fma(nom, zh0, sh0), wh);
-            z = fma(be, fma(nom, v0, z0), t);
-        }
-        const double q = fma(nal, s, r);
-        const double qh = fma(nal, sh, rh);
-        const double y = fma(nal, z, w);
-        c.ph[i] = ph;
-        c.s[i] = s;
-        c.sh[i] = sh;
-        c.z[i] = z;
-        c.q[i] = q;
-        c.qh[i] = qh;
-        c.y[i] = y;
-        c.zh[i] = __dmul_rn(z, d);
-        red.add(0, q, y);
-        red.add_sq(1, y);
+    if (P1Cfg<R>::pairs) {
+        for_pairs(c.n, [&](int64_t i, bool pair) {
+            if (pair) {
+                const double2 rh = ld2(c.rh, i), w = ld2(c.w, i), wh = ld2(c.wh, i), t = ld2(c.t, i),
+                              r = ld2(c.r, i), d = ld2(c.invd, i);
+                double2 ph{0.0, 0.0}, s{0.0, 0.0}, sh{0.0, 0.0}, z{0.0, 0.0}, zh{0.0, 0.0}, v{0.0, 0.0};
+                if (!first) {
+                    ph = ld2(c.ph, i);
+                    s = ld2(c.s, i);
+                    sh = ld2(c.sh, i);
+                    z = ld2(c.z, i);
+                    zh = ld2(c.zh, i);
+                    v = ld2(c.v, i);
+                }
+                const P1Out o0 = p1_elem(P1In{rh.x, w.x, wh.x, t.x, r.x, d.x, ph.x, s.x, sh.x, z.x, zh.x, v.x}, first,
+                                         nal, be, nom, red);
+                const P1Out o1 = p1_elem(P1In{rh.y, w.y, wh.y, t.y, r.y, d.y, ph.y, s.y, sh.y, z.y, zh.y, v.y}, first,
+                                         nal, be, nom, red);
+                st2(c.ph, i, make_double2(o0.ph, o1.ph));
+                st2(c.s, i, make_double2(o0.s, o1.s));
+                st2(c.sh, i, make_double2(o0.sh, o1.sh));
+                st2(c.z, i, make_double2(o0.z, o1.z));
+                st2(c.q, i, make_double2(o0.q, o1.q));
+                st2(c.qh, i, make_double2(o0.qh, o1.qh));
+                st2(c.y, i, make_double2(o0.y, o1.y));
+                st2(c.zh, i, make_double2(o0.zh, o1.zh));
+            } else {
+                p1_store(c, i, p1_elem(p1_load(c, i, first), first, nal, be, nom, red));
+            }
+        });
+    } else {
+        for (int64_t i = gtid(); i < c.n; i += gstride())
+            p1_store(c, i, p1_elem(p1_load(c, i, first), first, nal, be, nom, red));
     }
     __shared__ double vals[R::K];
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_pipe_omega(c.st, vals);
 }
 
+// (P3's launch shape: see P1Cfg.)
 template <class R> struct P3Cfg { static constexpr int blocks = 2, pairs = 1; };
 template <int K> struct P3Cfg<PlainR<K>> { static constexpr int blocks = 3, pairs = 0; };
 
