@@ -87,8 +87,10 @@ __global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k1(Ct
     if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
 }
 
-// K2: q = fma(-alpha, s, r), qhat = q * invd
-__global__ void __launch_bounds__(256) k_cls_k2(Ctx c) {
+// K2: q = fma(-alpha, s, r), qhat = q * invd. Four blocks per SM, like K4, whose
+// occupancy sizes the vector grid: left free, the compiler took 80 registers, three
+// blocks fit and the grid ran in 1.33 waves.
+__global__ void __launch_bounds__(256, 4) k_cls_k2(Ctx c) {
     if (c.st->done) return;
     const double na = -c.st->alpha;
     for_pairs(c.n, [&](int64_t i, bool pair) {
