@@ -4,7 +4,8 @@ Both the GPU parity tests and the oracle's tests draw their inputs from
 ``gen``, so these checks pin it to things other than itself:
 - the published SplitMix64 output sequence;
 - brute-force stencil constructions;
-- closed-form nonzero counts.
+- closed-form nonzero counts;
+- the exact rational sum for the ill-conditioned dots.
 """
 import numpy as np
 import pytest
@@ -119,3 +120,14 @@ def test_banded_counts_and_values(n, band):
                 assert D[i, j] == (-(1.0 - 1e-4) if j < i else -1.0)
             else:
                 assert D[i, j] == 0.0
+
+
+@pytest.mark.parametrize("cond", [1e16, 1e32, 1e48])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 10, 301])
+def test_ill_conditioned_dot_exact_value_is_the_rational_sum(cond, n):
+    from fractions import Fraction
+    for seed in range(3):
+        x, y, exact = gen.ill_conditioned_dot(n, cond, seed)
+        assert x.size == n and y.size == n and np.all(np.isfinite(x)) and np.all(np.isfinite(y))
+        assert sum(Fraction(a) * Fraction(b) for a, b in zip(x.tolist(), y.tolist())) == exact
+        assert exact != 0
