@@ -216,21 +216,7 @@ def run_gpu(args):
     value = world * iters / (ms * 1e-3)
     clocks = clk.summary()
 
-    # roofline of the dominant kernel: SpMV with its dot epilogue (classic K1, K3)
-    hbm, peak_kind = _peaks()
-    nl, kms = prof_tot.get("spmv_dot", [0, 0.0])
-    per_launch_ms = kms / max(nl, 1)
-    alg_bytes = 12 * A.nnz + 32 * A.n + 8
-    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9 if nl else None
-    shares = {k: round(v[1] / max(sum(t[1] for t in prof_tot.values()), 1e-12), 4)
-              for k, v in prof_tot.items()}
-    traffic = _traffic()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                "kernel": "SpMV + exact-dot epilogue (classic K1/K3)",
-                "alg_bytes_per_launch": alg_bytes, "launches": nl,
-                "avg_launch_us": per_launch_ms * 1e3, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "time_share": shares}
+    roofline = _roofline(A, prof_tot)
 
     if not args.extras:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -296,6 +282,43 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _roofline(A, prof_tot):
+    """Roofline of the dominant kernel -- the SpMV with its exact-dot epilogue,
+    classic K1 (<r0,s>) and K3 (<q,y>, <y,y>) -- from the library's CUDA events
+    over the timed solves. Only launches that ran are counted (the library
+    leaves out those that returned at once on the stop flag). Algorithmic bytes
+    per launch: 12 nnz (col + val) + 8 (n+1) (rowptr) + 8 n (x, ideal reuse)
+    + 8 n (the companion vector of the dot) + 8 n (output) = 12 nnz + 32 n + 8.
+    K4 (x and r updates with <r0,r>, <r,r>) moves 64 n bytes per launch."""
+    hbm, peak_kind = _peaks()
+    alg = 12 * A.nnz + 32 * A.n + 8
+    total_ms = max(sum(t[1] for t in prof_tot.values()), 1e-12)
+
+    def stat(names, byt):
+        nl = sum(prof_tot.get(k, [0, 0.0])[0] for k in names)
+        ms = sum(prof_tot.get(k, [0, 0.0])[1] for k in names)
+        if not nl:
+            return None
+        us = ms * 1e3 / nl
+        gbs = byt / (us * 1e-6) / 1e9
+        return {"launches": nl, "avg_launch_us": us, "achieved": gbs, "frac": gbs / hbm,
+                "time_share": ms / total_ms, "alg_bytes_per_launch": byt}
+
+    both = stat(["k1_spmv_dot", "k3_spmv_dot2"], alg)
+    per = {"K1 SpMV + <r0,s>": stat(["k1_spmv_dot"], alg),
+           "K3 SpMV + <q,y>, <y,y>": stat(["k3_spmv_dot2"], alg),
+           "K4 x, r + <r0,r>, <r,r>": stat(["k4_vec_dot2"], 64 * A.n),
+           "K2, K5 vector updates": stat(["vec"], 44 * A.n)}
+    return {"bound": "hbm", "achieved": both["achieved"] if both else None, "peak": hbm, "unit": "GB/s",
+            "frac": both["frac"] if both else None, "traffic": _traffic(),
+            "kernel": "SpMV + exact-dot epilogue (classic K1 and K3 launches)",
+            "alg_bytes_per_launch": alg, "launches": both["launches"] if both else 0,
+            "avg_launch_us": both["avg_launch_us"] if both else None,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+            "per_kernel": per,
+            "time_share": {k: round(v[1] / total_ms, 4) for k, v in prof_tot.items() if v[0]}}
 
 
 def _traffic():
@@ -476,12 +499,14 @@ def run_solve_only(args):
     variant = 1 if args.solve_only == "pipelined" else 0
     for _ in range(args.warmup):
         rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=variant, x_out=x, loop_mode=1)
-    tot, iters = {}, 0
+    tot, iters, traces = {}, 0, []
     torch.cuda.synchronize()
     t = time.perf_counter()
     for _ in range(args.steps):
         r = rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=variant, x_out=x, profile=True,
-                          loop_mode=1)
+                          loop_mode=1, trace=(1 << 15) if args.trace else 0)
+        if args.trace:
+            traces.append((r["iters"], r["trace"]))
         iters += r["iters"]
         for k, (nl, ms) in r["prof"].items():
             a = tot.setdefault(k, [0, 0.0])
@@ -489,11 +514,28 @@ def run_solve_only(args):
             a[1] += ms
     torch.cuda.synchronize()
     dt = time.perf_counter() - t
-    print(json.dumps({"variant": args.solve_only, "grid": GRID, "iters": iters,
-                      "iters_per_s": iters / dt,
-                      "us_per_launch": {k: v[1] * 1e3 / max(v[0], 1) for k, v in tot.items() if v[0]},
-                      "launches": {k: v[0] for k, v in tot.items() if v[0]}}), flush=True)
+    line = {"variant": args.solve_only, "grid": GRID, "iters": iters, "iters_per_s": iters / dt,
+            "us_per_launch": {k: v[1] * 1e3 / max(v[0], 1) for k, v in tot.items() if v[0]},
+            "launches": {k: v[0] for k, v in tot.items() if v[0]}}
+    if args.trace:
+        line["trace"] = _trace_buckets(traces)
+    print(json.dumps(line), flush=True)
     return 0
+
+
+def _trace_buckets(traces, width=25):
+    """Per-launch traces of several solves -> per kernel kind, the median
+    launch time (us) in buckets of `width` iterations (launches that ran only)."""
+    import collections
+    b = collections.defaultdict(list)
+    for iters, tr in traces:
+        for kind, it, ms in tr:
+            if 0 <= it < iters:
+                b[(kind, it // width)].append(ms * 1e3)
+    out = {}
+    for (kind, k), v in sorted(b.items()):
+        out.setdefault(kind, {})[f"{k * width}-{k * width + width - 1}"] = round(statistics.median(v), 1)
+    return out
 
 
 def run_micro_exdot(args):
@@ -547,6 +589,9 @@ def main():
     ap.add_argument("--solve-only", default=None, choices=["classic", "pipelined"],
                     help="only warm-up + timed solves of this variant on the --grid workload, "
                          "with per-kernel CUDA-event times (a profiling target)")
+    ap.add_argument("--trace", action="store_true",
+                    help="with --solve-only: per-launch CUDA-event trace, reported as per-kernel "
+                         "medians over buckets of 25 iterations")
     ap.add_argument("--micro-exdot", default=None, metavar="LOG2N:COND[,...]",
                     help="only the standalone exact-dot microbenchmark on these cases "
                          "(e.g. 24:1e32 or 20:1,27:1e48); the profiling target of the exdot")

@@ -202,15 +202,25 @@ typedef struct {
 } rbs_history;
 
 /* Kernel timing from rbs_opts.profile: per kernel kind, launches and summed
- * CUDA-event milliseconds over the whole solve. */
+ * CUDA-event milliseconds over the whole solve. The host enqueues iterations
+ * ahead of reading the stop flag, so a few launches return at once because the
+ * loop has already stopped: those (every launch of an iteration index >= iters,
+ * and the launches after the stopping kernel in the last iteration: classic K5,
+ * pipelined S18) are left out of launches/ms. The optional per-launch trace
+ * lists every launch in enqueue order, left-out ones included. */
 #define RBS_PROF_KINDS 8
 typedef struct {
     int64_t launches[RBS_PROF_KINDS];
     double ms[RBS_PROF_KINDS];
-    /* kinds: 0 SpMV with a dot epilogue (classic K1, K3), 1 vector update
-       without dots (classic K2, K5), 2 set-up, 3 standalone SpMV (pipelined
-       S10/S18), 4 vector update with dots (classic K4, pipelined P1, P3),
-       5..7 unused */
+    /* kinds: 0 classic K1 (SpMV + <r0,s>), 1 vector update without dots
+       (classic K2, K5), 2 set-up, 3 standalone SpMV (pipelined S10/S18),
+       4 pipelined vector update with dots (P1, P3), 5 classic K3 (SpMV +
+       <q,y>, <y,y>), 6 classic K4 (x, r update + <r0,r>, <r,r>), 7 unused */
+    int32_t trace_cap;   /* entries of the three trace arrays (0 or null arrays: no trace) */
+    int32_t trace_len;   /* entries written (at most trace_cap) */
+    int32_t *trace_kind; /* host: kernel kind of each launch */
+    int32_t *trace_iter; /* host: iteration index of the launch, -1 for set-up */
+    float *trace_ms;     /* host: the launch's CUDA-event duration in milliseconds */
 } rbs_prof;
 
 /* Solve A x = b with Jacobi-preconditioned BiCGStab (Fig. 2) or pipelined

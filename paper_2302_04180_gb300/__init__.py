@@ -30,7 +30,7 @@ RBS_LIMBS = 136
 RBS_NOALLOC_MAX_DOTS = 6
 RBS_HIST_W = 12
 RBS_PROF_KINDS = 8
-PROF_KIND_NAMES = ("spmv_dot", "vec", "setup", "spmv", "vec_dot")
+PROF_KIND_NAMES = ("k1_spmv_dot", "vec", "setup", "spmv", "pipe_vec_dot", "k3_spmv_dot2", "k4_vec_dot2")
 
 # every symbol include/rbs.h declares
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
@@ -74,7 +74,9 @@ class _Hist(C.Structure):
 
 
 class _Prof(C.Structure):
-    _fields_ = [("launches", C.c_int64 * RBS_PROF_KINDS), ("ms", C.c_double * RBS_PROF_KINDS)]
+    _fields_ = [("launches", C.c_int64 * RBS_PROF_KINDS), ("ms", C.c_double * RBS_PROF_KINDS),
+                ("trace_cap", C.c_int32), ("trace_len", C.c_int32), ("trace_kind", C.c_void_p),
+                ("trace_iter", C.c_void_p), ("trace_ms", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -306,10 +308,13 @@ def rbs_jacobi_apply(invd, p, phat=None, stream=None):
 
 def rbs_solve(A, b, x0=None, jacobi_diag=None, tol=1e-8, maxit=1000, variant=RBS_CLASSIC,
               x_out=None, history=True, dot_mode=RBS_DOT_EXACT, check_every=0,
-              profile=False, loop_mode=0, stream=None, raise_on_status=False):
+              profile=False, loop_mode=0, stream=None, raise_on_status=False, trace=0):
     """Reproducible PBiCGStab (variant 0, Fig. 2) or p-PBiCGStab (variant 1, Fig. 4).
     Returns a dict: x, iters, converged, status, tau0, tau_final, rho0, tau_max,
-    alpha0, mu0, hist (iters x 12 float64) and prof (per kernel kind)."""
+    alpha0, mu0, hist (iters x 12 float64) and prof (per kernel kind: launches
+    and milliseconds of the launches that ran). With profile and trace = N > 0,
+    also trace: up to N per-launch (kind name, iteration, ms) tuples in enqueue
+    order."""
     n = int(A.n)
     if x_out is None:
         if isinstance(b, np.ndarray):
@@ -323,6 +328,13 @@ def rbs_solve(A, b, x0=None, jacobi_diag=None, tol=1e-8, maxit=1000, variant=RBS
     info = _Info()
     opts = _Opts(int(dot_mode), int(check_every), 1 if profile else 0, int(loop_mode))
     prof = _Prof()
+    tcap = int(trace) if profile else 0
+    t_kind = np.zeros(max(tcap, 1), dtype=np.int32)
+    t_iter = np.zeros(max(tcap, 1), dtype=np.int32)
+    t_ms = np.zeros(max(tcap, 1), dtype=np.float32)
+    if tcap > 0:
+        prof.trace_cap = tcap
+        prof.trace_kind, prof.trace_iter, prof.trace_ms = t_kind.ctypes.data, t_iter.ctypes.data, t_ms.ctypes.data
     csr = _csr(A)
     rc = load().rbs_solve_ex(C.byref(csr), _ptr(b), _ptr(x0), _ptr(jacobi_diag), float(tol),
                              int(maxit), int(variant), C.byref(opts), _ptr(x_out),
@@ -337,6 +349,8 @@ def rbs_solve(A, b, x0=None, jacobi_diag=None, tol=1e-8, maxit=1000, variant=RBS
         "hist": rec[: h.len].copy() if history else None,
         "prof": {PROF_KIND_NAMES[k]: (int(prof.launches[k]), float(prof.ms[k]))
                  for k in range(len(PROF_KIND_NAMES))} if profile else None,
+        "trace": [(PROF_KIND_NAMES[int(t_kind[j])] if 0 <= t_kind[j] < len(PROF_KIND_NAMES) else str(int(t_kind[j])),
+                   int(t_iter[j]), float(t_ms[j])) for j in range(prof.trace_len)] if tcap > 0 else None,
     }
 
 

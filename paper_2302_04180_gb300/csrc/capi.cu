@@ -266,12 +266,19 @@ int window_param() {
 // Per-kernel CUDA events. Kernels enqueued back to back share events: a
 // kernel's start is the previous kernel's end, so each launch records one
 // event; gap() marks other work in between (the next start is recorded anew).
+// Each record carries the loop iteration it belongs to (-1: set-up) and its
+// position within that iteration's launches.
 struct EventTimer : KernelTimer {
+    struct Rec {
+        int kind, iter, slot;
+        cudaEvent_t a, b;
+    };
     Workspace *w;
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> rec;
+    std::vector<Rec> rec;
     size_t used = 0;
     cudaEvent_t last_end = nullptr;
     cudaError_t err = cudaSuccess;
+    int iter = -1, slot = 0;
     explicit EventTimer(Workspace *ws) : w(ws) {}
     cudaEvent_t take() {
         if (used == w->evpool.size()) {
@@ -285,6 +292,10 @@ struct EventTimer : KernelTimer {
         }
         return w->evpool[used++];
     }
+    void begin_iteration(int j) {
+        iter = j;
+        slot = 0;
+    }
     void before(int kind) override {
         cudaEvent_t a = last_end;
         if (!a) {
@@ -292,7 +303,7 @@ struct EventTimer : KernelTimer {
             if (!a) return;
             cudaEventRecord(a, w->stream);
         }
-        rec.push_back({kind, {a, nullptr}});
+        rec.push_back({kind, iter, slot++, a, nullptr});
     }
     void after(int kind) override {
         (void)kind;
@@ -300,7 +311,7 @@ struct EventTimer : KernelTimer {
         last_end = nullptr;
         if (!b || rec.empty()) return;
         cudaEventRecord(b, w->stream);
-        rec.back().second.second = b;
+        rec.back().b = b;
         last_end = b;
     }
     void gap() override { last_end = nullptr; }
@@ -577,7 +588,15 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
     if (opts) o = *opts;
     if (o.dot_mode != RBS_DOT_EXACT && o.dot_mode != RBS_DOT_PLAIN) return fail(RBS_EINVAL, "bad dot_mode");
     if (o.loop_mode != RBS_LOOP_GRAPH && o.loop_mode != RBS_LOOP_HOST) return fail(RBS_EINVAL, "bad loop_mode");
-    if (prof) memset(prof, 0, sizeof *prof);
+    if (prof) {
+        // keep the caller's trace buffers, clear the counters
+        rbs_prof keep = *prof;
+        memset(prof, 0, sizeof *prof);
+        prof->trace_cap = keep.trace_cap;
+        prof->trace_kind = keep.trace_kind;
+        prof->trace_iter = keep.trace_iter;
+        prof->trace_ms = keep.trace_ms;
+    }
 
     Workspace *w;
     if ((rc = ws_get((cudaStream_t)stream, &w))) return rc;
@@ -642,14 +661,20 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         const int sb = block_of(p_spmv_block.load(), 256);
         a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve, smode & SPMV_MODE_MASK));
         a.spmv.mode = smode;
+        a.k3 = variant == RBS_CLASSIC
+                   ? grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 3, sb, carve, smode & SPMV_MODE_MASK))
+                   : a.spmv;
+        a.k3.mode = smode;
         a.carveout = carveout_param();
         a.spmv.carveout = a.carveout;
+        a.k3.carveout = a.carveout;
         // window headroom: at most 2^20 products per thread per launch
         const int64_t minv = (n + ((int64_t)a.vec.block << 20) - 1) / ((int64_t)a.vec.block << 20);
         if (a.vec.grid < minv) a.vec.grid = (int)minv;
         if (a.p3.grid < minv) a.p3.grid = (int)minv;
         const int64_t mins = (n + ((int64_t)a.spmv.block << 20) - 1) / ((int64_t)a.spmv.block << 20);
         if (a.spmv.grid < mins) a.spmv.grid = (int)mins;
+        if (a.k3.grid < mins) a.k3.grid = (int)mins;
     }
 
     // structure check and Jacobi set-up (Sec. 4: M = diag(A))
@@ -683,7 +708,10 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
         int cur = -1;
         if (launched < maxit) {
             int m = (int)((maxit - launched) < chunk ? (maxit - launched) : chunk);
-            for (int i = 0; i < m; i++) CK(solver_iteration(a, variant, w->stream, tm));
+            for (int i = 0; i < m; i++) {
+                if (tm) timer.begin_iteration((int)(launched + i));
+                CK(solver_iteration(a, variant, w->stream, tm));
+            }
             launched += m;
             cur = slot;
             CK(cudaMemcpyAsync(&w->h_flags[cur], &w->st->done, sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -725,13 +753,25 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
                            is_device_ptr(x_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, w->stream));
     CK(cudaStreamSynchronize(w->stream));
     if (tm) {
+        // launches that returned at once on the stop flag are traced but not
+        // counted: every launch of an iteration index >= iters, and in the last
+        // iteration those after the stopping kernel (classic K5, pipelined S18)
+        const int last_slot = variant == RBS_CLASSIC ? 4 : 3;
+        const bool trace = prof->trace_cap > 0 && prof->trace_kind && prof->trace_iter && prof->trace_ms;
         for (auto &r : timer.rec) {
-            if (!r.second.second) continue;
+            if (!r.b) continue;
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess &&
-                r.first < RBS_PROF_KINDS) {
-                prof->ms[r.first] += ms;
-                prof->launches[r.first] += 1;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) continue;
+            if (trace && prof->trace_len < prof->trace_cap) {
+                prof->trace_kind[prof->trace_len] = r.kind;
+                prof->trace_iter[prof->trace_len] = r.iter;
+                prof->trace_ms[prof->trace_len] = ms;
+                prof->trace_len++;
+            }
+            const bool ran = r.iter < h->iter && !(r.iter == h->iter - 1 && r.slot == last_slot && h->done);
+            if (ran && r.kind >= 0 && r.kind < RBS_PROF_KINDS) {
+                prof->ms[r.kind] += ms;
+                prof->launches[r.kind] += 1;
             }
         }
     }

@@ -458,12 +458,12 @@ static cudaError_t iter_t(const SolverArgs &a, int variant, cudaStream_t s, Kern
     Ctx c = make_ctx(a);
     if (variant == RBS_CLASSIC) {
         const bool lng = (a.spmv.mode & SPMV_MODE_MASK) == SPMV_MODE_LONG;
-        if (lng) TIMED(PK_SPMV_DOT, (k_cls_k1<R1, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
-        else TIMED(PK_SPMV_DOT, (k_cls_k1<R1, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        if (lng) TIMED(PK_K1, (k_cls_k1<R1, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
+        else TIMED(PK_K1, (k_cls_k1<R1, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k2<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
-        if (lng) TIMED(PK_SPMV_DOT, (k_cls_k3<R2, SPMV_CAP_LONG><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
-        else TIMED(PK_SPMV_DOT, (k_cls_k3<R2, SPMV_CAP_SHORT><<<a.spmv.grid, a.spmv.block, 0, s>>>(c)));
-        TIMED(PK_VEC_DOT, (k_cls_k4<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
+        if (lng) TIMED(PK_K3, (k_cls_k3<R2, SPMV_CAP_LONG><<<a.k3.grid, a.k3.block, 0, s>>>(c)));
+        else TIMED(PK_K3, (k_cls_k3<R2, SPMV_CAP_SHORT><<<a.k3.grid, a.k3.block, 0, s>>>(c)));
+        TIMED(PK_K4, (k_cls_k4<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
         TIMED(PK_VEC, (k_cls_k5<<<a.vec.grid, a.vec.block, 0, s>>>(c)));
     } else {
         TIMED(PK_VEC_DOT, (k_pipe_p1<R2><<<a.vec.grid, a.vec.block, 0, s>>>(c)));
@@ -541,36 +541,38 @@ int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int ca
     apply_carveout(dot_mode, carveout);
     if (which == 0 && variant == RBS_PIPELINED) return spmv_blocks_per_sm(block, carveout, spmv_mode);
     const bool lng = spmv_mode == SPMV_MODE_LONG;
-    int nb = 0, nb2 = 0;
+    int nb = 0;
     cudaError_t e = cudaSuccess;
     if (dot_mode == RBS_DOT_PLAIN) {
+        using R1 = PlainR<1>;
+        using R2 = PlainR<2>;
         if (which == 0) {
-            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<PlainR<1>, SPMV_CAP_LONG>, block, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<PlainR<1>, SPMV_CAP_SHORT>, block, 0);
-            if (e == cudaSuccess)
-                e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<PlainR<2>, SPMV_CAP_LONG>, block, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<PlainR<2>, SPMV_CAP_SHORT>, block,
-                                                                        0);
-            nb = nb2 < nb ? nb2 : nb;
+            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<R1, SPMV_CAP_LONG>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<R1, SPMV_CAP_SHORT>, block, 0);
+        } else if (which == 3) {
+            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k3<R2, SPMV_CAP_LONG>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k3<R2, SPMV_CAP_SHORT>, block, 0);
         } else if (variant == RBS_PIPELINED) {
             e = which == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<PlainR<5>>, block, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p1<PlainR<2>>, block, 0);
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p1<R2>, block, 0);
         } else {
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<PlainR<2>>, block, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<R2>, block, 0);
         }
-    } else if (which == 0) {
-        e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<ExactR<1, SQ>, SPMV_CAP_LONG>, block, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<ExactR<1, SQ>, SPMV_CAP_SHORT>, block, 0);
-        if (e == cudaSuccess)
-            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<ExactR<2, SQ>, SPMV_CAP_LONG>, block, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_cls_k3<ExactR<2, SQ>, SPMV_CAP_SHORT>, block,
-                                                                    0);
-        nb = nb2 < nb ? nb2 : nb;
-    } else if (variant == RBS_PIPELINED) {
-        e = which == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, block, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p1<ExactR<2, SQ>>, block, 0);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<ExactR<2, SQ>>, block, 0);
+        using R1 = ExactR<1, SQ>;
+        using R2 = ExactR<2, SQ>;
+        if (which == 0) {
+            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<R1, SPMV_CAP_LONG>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k1<R1, SPMV_CAP_SHORT>, block, 0);
+        } else if (which == 3) {
+            e = lng ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k3<R2, SPMV_CAP_LONG>, block, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k3<R2, SPMV_CAP_SHORT>, block, 0);
+        } else if (variant == RBS_PIPELINED) {
+            e = which == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p3<ExactR<5, SQ>>, block, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pipe_p1<R2>, block, 0);
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cls_k4<R2>, block, 0);
+        }
     }
     if (e != cudaSuccess || nb < 1) nb = 1;
     return nb;

@@ -79,10 +79,11 @@ struct SolverArgs {
     int carveout;  // shared-memory carveout percent for staging kernels, -1 = driver default
     Cfg vec, spmv;
     Cfg p3;  // the pipelined P3 kernel, sized from its own occupancy
+    Cfg k3;  // the classic K3 kernel (SpMV + two dots), sized from its own occupancy
 };
 
 // Kernel kinds for profiling (rbs_prof.kinds).
-enum ProfKind { PK_SPMV_DOT = 0, PK_VEC = 1, PK_SETUP = 2, PK_SPMV = 3, PK_VEC_DOT = 4 };
+enum ProfKind { PK_K1 = 0, PK_VEC = 1, PK_SETUP = 2, PK_SPMV = 3, PK_VEC_DOT = 4, PK_K3 = 5, PK_K4 = 6 };
 
 struct KernelTimer {
     virtual void before(int kind) = 0;
@@ -129,7 +130,8 @@ cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, const in
 int batch_max_clusters(int csize);
 
 // occupancy-derived persistent grid for the kernels of one kind: which = 0 the
-// SpMV kernels, 1 the vector kernels, 2 the pipelined P3 kernel
+// SpMV kernels (classic K1, pipelined S10/S18), 1 the vector kernels, 2 the
+// pipelined P3 kernel, 3 the classic K3 kernel
 int solver_blocks_per_sm(int variant, int dot_mode, int which, int block, int carveout, int spmv_mode);
 // Resident blocks per SM of the standalone SpMV kernel at this block size and
 // shared-memory carveout (applies the carveout first).

@@ -137,7 +137,7 @@ struct ExactS {
             const long long d = pp[j * NT] - pn[j * NT];
             pp[j * NT] = 0;
             pn[j * NT] = 0;
-            if (d) atomicAdd(&sacc[k][a[k] + j], (unsigned long long)d);
+            if (d) sacc_add(&sacc[k][a[k] + j], d);
         }
     }
     __device__ __forceinline__ void add(int k, double x, double y) {
@@ -184,7 +184,7 @@ struct ExactS {
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < 2 * W; j++) win[(k * 2 * W + j) * NT + threadIdx.x] = 0;
-        if (sum && lo + lane < NL) atomicAdd(&sacc[k][lo + lane], (unsigned long long)sum);
+        if (sum && lo + lane < NL) sacc_add(&sacc[k][lo + lane], sum);
         a[k] = WIN_EMPTY;
     }
     template <int SCRATCH = 0>
