@@ -131,3 +131,22 @@ def test_ill_conditioned_dot_exact_value_is_the_rational_sum(cond, n):
         assert x.size == n and y.size == n and np.all(np.isfinite(x)) and np.all(np.isfinite(y))
         assert sum(Fraction(a) * Fraction(b) for a, b in zip(x.tolist(), y.tolist())) == exact
         assert exact != 0
+
+
+def test_full_size_digests_are_complete():
+    """The stored oracle digests of the full-size solves (written by
+    tests/golden/make_c3_digests.py) list every iteration's tau and converge."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_c3_digests as D
+    for name in D.WORKLOADS:
+        d = D.read(name)
+        it = int(d["iters"])
+        assert it > 100 and int(d["status"]) == 0 and int(d["converged"]) == 1
+        assert sorted(d["tau"]) == list(range(it))
+        assert len(d["history_sha256"]) == 64 and len(d["x_sha256"]) == 64
+        # tau falls below tau_max exactly at the last iteration (the stop test)
+        tau = [np.array([int(d["tau"][j], 16)], dtype=np.uint64).view(np.float64)[0] for j in range(it)]
+        tmax = np.array([int(d["tau_max"], 16)], dtype=np.uint64).view(np.float64)[0]
+        assert tau[-1] <= tmax and all(t > tmax for t in tau[:-1])
