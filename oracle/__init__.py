@@ -45,8 +45,12 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(d) <= so_t for d in deps):
             return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", *CFLAGS, "-o", tmp, *srcs, "-lm"]
-    subprocess.run(cmd, check=True, cwd=_HERE)
+    # OpenMP for the threaded oracle (set_threads); without it the oracle is
+    # sequential and the thread count is ignored
+    r = subprocess.run(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, *srcs, "-lm"], cwd=_HERE,
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, *srcs, "-lm"], check=True, cwd=_HERE)
     os.replace(tmp, _SO)
     return _SO
 
@@ -87,6 +91,10 @@ def _load():
             lib.orc_jacobi_invd.argtypes = [C.c_int64, lp, ip, dp, dp, dp]
             lib.orc_jacobi_apply.restype = None
             lib.orc_jacobi_apply.argtypes = [C.c_int64, dp, dp, dp]
+            lib.orc_set_threads.restype = None
+            lib.orc_set_threads.argtypes = [C.c_int]
+            lib.orc_get_threads.restype = C.c_int
+            lib.orc_get_threads.argtypes = []
             lib.orc_solve.restype = C.c_int
             lib.orc_solve.argtypes = [C.c_int64, lp, ip, dp, dp, dp, dp,
                                       C.c_double, C.c_int32, C.c_int32, dp,
@@ -120,6 +128,16 @@ def twoprod(a: float, b: float):
 
 def mul_add_unfused(a: float, b: float, c: float) -> float:
     return _load().orc_mul_add_unfused(a, b, c)
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's loops and exact dots (1: sequential; results do
+    not depend on it)."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def exdot(x, y) -> float:

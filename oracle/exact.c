@@ -18,6 +18,7 @@
 #include "oracle.h"
 
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 /* ---- Alg. 1 and Alg. 2 --------------------------------------------------- */
@@ -186,7 +187,35 @@ static double round_digits(const uint32_t *src, int32_t flags) {
 
 double orc_acc_round(const orc_acc *a) { return round_digits(a->d, a->flags); }
 
+static int orc_threads = 1;
+
+void orc_set_threads(int n) { orc_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return orc_threads; }
+
+/* One exact dot over threads: thread t accumulates its contiguous chunk into
+ * its own digit array (orc_exdot_limbs), the integer arrays are summed and the
+ * total rounded once (orc_round_limbs). */
+static double exdot_threads(const double *x, const double *y, int64_t n, int T) {
+    int64_t(*limbs)[ORC_DIGITS] = calloc((size_t)T, sizeof *limbs);
+    int32_t *flags = calloc((size_t)T, sizeof *flags);
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+    for (int t = 0; t < T; t++) {
+        const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+        orc_exdot_limbs(x + lo, y + lo, hi - lo, limbs[t], &flags[t]);
+    }
+    int64_t sum[ORC_DIGITS] = {0};
+    int32_t fl = 0;
+    for (int t = 0; t < T; t++) {
+        for (int d = 0; d < ORC_DIGITS; d++) sum[d] += limbs[t][d];
+        fl |= flags[t];
+    }
+    free(limbs);
+    free(flags);
+    return orc_round_limbs(sum, fl);
+}
+
 double orc_exdot(const double *x, const double *y, int64_t n) {
+    if (orc_threads > 1) return exdot_threads(x, y, n, orc_threads);
     orc_acc a;
     orc_acc_zero(&a);
     for (int64_t i = 0; i < n; i++) orc_acc_add_product(&a, x[i], y[i]);

@@ -73,6 +73,15 @@ double orc_round_limbs(const int64_t *limbs, int32_t flags);
 
 /* SpMV in CSR with the row's fma chain in stored order, starting at +0.0
  * (Sec. 4.1, "Sparse matrix-vector product"; Sec. 3.3). */
+/* Threads the oracle's loops and exact dots use (1, the default: sequential).
+ * With more, SpMV rows and element-wise steps are split across threads (each
+ * element is computed exactly as before), and each exact dot sums per-thread
+ * orc_exdot_limbs integers before its one rounding (orc_round_limbs): the
+ * rank-split reduction, so every result is bitwise that of one thread. Built
+ * without OpenMP, the count is ignored. */
+void orc_set_threads(int n);
+int orc_get_threads(void);
+
 void orc_spmv(int64_t n, const int64_t *rowptr, const int32_t *col,
               const double *val, const double *x, double *y);
 

@@ -53,6 +53,7 @@ static double orc_qnan(void) {
 
 void orc_spmv(int64_t n, const int64_t *rowptr, const int32_t *col,
               const double *val, const double *x, double *y) {
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
     for (int64_t i = 0; i < n; i++) {
         double acc = 0.0;
         for (int64_t k = rowptr[i]; k < rowptr[i + 1]; k++)
@@ -85,6 +86,7 @@ int orc_jacobi_invd(int64_t n, const int64_t *rowptr, const int32_t *col,
 
 void orc_jacobi_apply(int64_t n, const double *invd, const double *p,
                       double *phat) {
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
     for (int64_t i = 0; i < n; i++) phat[i] = p[i] * invd[i];
 }
 
@@ -113,8 +115,10 @@ static int solve_classic(int64_t n, const int64_t *rowptr, const int32_t *col,
     /* set-up (Fig. 2, first rows) */
     if (x0) {
         orc_spmv(n, rowptr, col, val, x0, y);
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) { x[i] = x0[i]; r[i] = b[i] - y[i]; }
     } else {
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
     }
     memcpy(r0, r, (size_t)n * sizeof(double));
@@ -140,6 +144,7 @@ static int solve_classic(int64_t n, const int64_t *rowptr, const int32_t *col,
         double alpha = rho / sigma;
         if (!isfinite(alpha)) { status = ORC_ENAN; break; }
         /* S4, S5, S6 */
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) q[i] = fma(-alpha, s[i], r[i]);
         orc_jacobi_apply(n, invd, q, qh);
         orc_spmv(n, rowptr, col, val, qh, y);
@@ -148,6 +153,7 @@ static int solve_classic(int64_t n, const int64_t *rowptr, const int32_t *col,
         double delta = orc_exdot(y, y, n);
         double omega = (delta == 0.0) ? 0.0 : gamma / delta;
         /* S8, S9 */
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) {
             x[i] = fma(omega, qh[i], fma(alpha, ph[i], x[i]));
             r[i] = fma(-omega, y[i], q[i]);
@@ -175,6 +181,7 @@ static int solve_classic(int64_t n, const int64_t *rowptr, const int32_t *col,
         rec[8] = beta;
         if (h) memcpy(h, rec, sizeof rec);
         if (!isfinite(beta)) { status = ORC_ENAN; break; }
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) {
             double t = fma(-omega, s[i], p[i]);
             p[i] = fma(beta, t, r[i]);
@@ -199,8 +206,10 @@ static int solve_pipelined(int64_t n, const int64_t *rowptr, const int32_t *col,
     /* set-up (Fig. 4, first rows) */
     if (x0) {
         orc_spmv(n, rowptr, col, val, x0, y);
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) { x[i] = x0[i]; r[i] = b[i] - y[i]; }
     } else {
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) { x[i] = 0.0; r[i] = b[i]; }
     }
     memcpy(r0, r, (size_t)n * sizeof(double));
@@ -233,6 +242,7 @@ static int solve_pipelined(int64_t n, const int64_t *rowptr, const int32_t *col,
         double rec[ORC_HIST_W];
         for (int k = 0; k < ORC_HIST_W; k++) rec[k] = orc_qnan();
         /* S1-S4 (copies at j = 0), S5-S7 */
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) {
             if (j == 0) {
                 ph[i] = rh[i]; s[i] = w[i]; sh[i] = wh[i]; z[i] = t[i];
@@ -256,6 +266,7 @@ static int solve_pipelined(int64_t n, const int64_t *rowptr, const int32_t *col,
         /* S11 */
         omega = (delta == 0.0) ? 0.0 : gamma / delta;
         /* S12-S15 */
+#pragma omp parallel for if (orc_get_threads() > 1) num_threads(orc_get_threads()) schedule(static)
         for (int64_t i = 0; i < n; i++) {
             x[i] = fma(omega, qh[i], fma(alpha, ph[i], x[i]));
             r[i] = fma(-omega, y[i], q[i]);
