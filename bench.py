@@ -115,24 +115,61 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _cpu_model():
+    import platform
+    impl = part = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key in ("model name", "cpu model"):
+                return line.split(":", 1)[1].strip()
+            if key == "cpu implementer":
+                impl = line.split(":", 1)[1].strip()
+            if key == "cpu part":
+                part = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    if part:
+        return f"{platform.machine()} (CPU implementer {impl}, part {part})"
+    return platform.machine()
+
+
 def _cpu_baseline(A, b, iters=2):
+    """The CPU oracle on a bounded sample of the benchmark solve (set-up and the
+    first iterations): on all host cores (the threaded oracle: rows split over
+    threads, exact dots merged as integers, bitwise the one-thread result) and
+    on one thread."""
     import oracle
     oracle.build()
-    t = time.perf_counter()
-    o = oracle.solve(A, b, tol=TOL, maxit=iters, variant=0, history=False)
-    dt = time.perf_counter() - t
-    return {"value": o["iters"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"set-up + {o['iters']} classic iterations of the same 256^3 solve, "
-                      f"single-threaded C oracle ({dt:.1f} s)"}
+    cores = os.cpu_count() or 1
+    legs = {}
+    for T, its in ((cores, 4 * iters), (1, iters)):
+        oracle.set_threads(T)
+        t = time.perf_counter()
+        o = oracle.solve(A, b, tol=TOL, maxit=its, variant=0, history=False)
+        legs[T] = (o["iters"], time.perf_counter() - t)
+    oracle.set_threads(1)
+    (ia, da), (i1, d1) = legs[cores], legs[1]
+    return {"value": ia / da, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": _cpu_model(),
+            "sample": f"set-up + {ia} classic iterations of the same {GRID}^3 solve, threaded C oracle on "
+                      f"{cores} threads ({da:.1f} s)",
+            "single_thread": {"value": i1 / d1, "unit": UNIT, "cores": 1,
+                              "sample": f"set-up + {i1} iterations, one thread ({d1:.1f} s)"}}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle (this method has no other
+    implementation to run) on the host cores, the same workload; each step a
+    bounded sample of it (set-up and one iteration)."""
     world, rank, _ = _dist()
     if world > 1 and rank != 0:
         return 0
     from paper_2302_04180_gb300 import gen
     import oracle
     oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     A = gen.poisson3d(GRID)
     b = oracle.spmv(A, np.ones(A.n))
     per = 1
@@ -148,9 +185,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _workload_config(A),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
                              "sample": f"per step: set-up + {per} classic iteration of the "
-                                       f"{GRID}^3 solve, single-threaded C oracle"},
+                                       f"{GRID}^3 solve, threaded C oracle on {cores} threads"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -244,28 +281,52 @@ def run_gpu(args):
         e_iters += rbs.rbs_solve(Ah, bh, tol=TOL, maxit=MAXIT, variant=0, x_out=xh, history=False)["iters"]
     e_dt = time.perf_counter() - t
     h2d = 8 * (A.n + 1) + 4 * A.nnz + 8 * A.nnz + 8 * A.n
+    # the copies alone (same bytes, same pinned buffers, one stream): the share
+    # of the end-to-end step that is host<->device traffic
+    scratch = [torch.empty_like(t_, device=dev) for t_ in (rp, cl, vl, bh)]
+    xd = torch.empty(A.n, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        for src, dst in zip((rp, cl, vl, bh), scratch):
+            dst.copy_(src, non_blocking=True)
+        xh.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+    c_dt = (time.perf_counter() - t) / e2e_steps
+    del scratch, xd
     e2e = {"value": world * e_iters / e_dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": 8 * A.n + 4, "path": "rbs_solve on pinned host buffers"}
+           "d2h_bytes_per_step": 8 * A.n + 4, "path": "rbs_solve on pinned host buffers",
+           "s_per_step": e_dt / e2e_steps, "copy_s_per_step": c_dt,
+           "copy_GB_per_s": (h2d + 8 * A.n) / c_dt / 1e9}
 
-    # comparators on the same workload (one solve each)
-    def once(**kw):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rr = solve(**kw)
-        torch.cuda.synchronize()
-        return rr, time.perf_counter() - t0
+    # the plain comparator and the pipelined variant on the same workload
+    plain = _comparator(rbs, Ad, b, x, dev)
+    rq_ = solve(variant=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rq_ = solve(variant=1)
+    torch.cuda.synchronize()
+    pipelined = {"value": rq_["iters"] / (time.perf_counter() - t0), "iters": rq_["iters"],
+                 "converged": rq_["converged"]}
 
-    rp_, tp_ = once(dot_mode=1)
-    rq_, tq_ = once(variant=1)
-    r2, t2 = once()
-    plain = {"value": rp_["iters"] / tp_, "iters": rp_["iters"], "converged": rp_["converged"],
-             "what": "same loop, binary64 dots with atomic accumulation (non-reproducible)"}
-    repro_one = r2["iters"] / t2
-    pipelined = {"value": rq_["iters"] / tq_, "iters": rq_["iters"], "converged": rq_["converged"]}
+    # inputs of the exact-dot grid, generated on the host cores meanwhile
+    import tempfile
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+    tmp = tempfile.mkdtemp(prefix="rbs_exdot_")
+    cases = [(lg, cond, seed) for lg in EXDOT_LOG2N for cond in EXDOT_CONDS
+             for seed in (EXDOT_SEEDS if lg < 27 else (0,))]
+    pool = ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4), mp_context=mp.get_context("spawn"))
+    futs = {c: pool.submit(_gen_dot_case, c[0], c[1], c[2], tmp) for c in cases}
 
-    kernels = _kernel_micro(rbs, gen, dev)
+    c1 = _c1(rbs, gen, dev)
+    c3b = _c3b(rbs, gen, dev)
     batched = _batched(rbs, gen, dev)
-    serving = _serving(rbs, gen, dev)
+    kernels = _kernel_micro(rbs, gen, dev, futs)
+    pool.shutdown()
+    import shutil
+    shutil.rmtree(tmp, ignore_errors=True)
+    serving = _serving(rbs, gen, dev, rates=(300.0, 600.0, 2000.0))
     gpu_launches = sum(v[0] for v in prof_tot.values())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -273,15 +334,87 @@ def run_gpu(args):
             "config": {**_workload_config(A), "iters_per_solve": r["iters"],
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
-            "plain_comparator": {**plain, "repro_over_plain_time": plain["value"] / repro_one},
-            "pipelined": pipelined, "kernels": kernels, "batched": batched,
-            "serving": serving}
+            "plain_comparator": plain,
+            "pipelined": pipelined, "c1_poisson16": c1, "c3b_convdiff192": c3b, "kernels": kernels,
+            "batched": batched, "serving": serving}
     if args.cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(A, b.cpu().numpy())
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+DRIFT_ITERS = (1, 10, 50, 100, 200, 400)
+
+
+def _hex(v):
+    return f"{int(np.array([v], dtype=np.float64).view(np.uint64)[0]):016x}"
+
+
+def _runs(rbs, Ad, b, x, dot_mode, reps, variant=0, tol=TOL):
+    """reps solves of one system (graph loop); per run: iterations, tau (hex)
+    at DRIFT_ITERS, tau_final and a digest of x (hex), and the wall time."""
+    import hashlib
+    import torch
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = rbs.rbs_solve(Ad, b, tol=tol, maxit=MAXIT, variant=variant, x_out=x, dot_mode=dot_mode)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        col = 7 if variant == 0 else 8
+        taus = {j: _hex(r["hist"][j - 1, col]) for j in DRIFT_ITERS if j <= r["iters"]}
+        xd = hashlib.sha256(x.cpu().numpy().tobytes()).hexdigest()[:16]
+        out.append({"iters": r["iters"], "tau": taus, "tau_final": _hex(r["tau_final"]), "x": xd,
+                    "s": dt, "converged": r["converged"]})
+    return out
+
+
+def _drift_summary(runs):
+    pats = {(r["iters"], tuple(sorted(r["tau"].items())), r["tau_final"], r["x"]) for r in runs}
+    return {"runs": len(runs), "distinct_results": len(pats),
+            "distinct_iters": sorted({r["iters"] for r in runs}),
+            "distinct_tau_at": {str(j): len({r["tau"].get(j) for r in runs if j in r["tau"]})
+                                for j in DRIFT_ITERS},
+            "distinct_x": len({r["x"] for r in runs})}
+
+
+def _comparator(rbs, Ad, b, x, dev, reps=10):
+    """The plain non-reproducible comparator (binary64 dots, atomic
+    accumulation across blocks) against the reproducible solve on the same
+    workload: both timed as the median of `reps` solves, and the run-to-run
+    drift of each (Table 4 style: iteration counts, tau at fixed iterations,
+    x). Also on a small system (Poisson 32^3), where the plain dots' block
+    order changes more of the rounding."""
+    plain = _runs(rbs, Ad, b, x, 1, reps)
+    exact = _runs(rbs, Ad, b, x, 0, max(5, reps // 2))
+    tp = statistics.median(r["s"] for r in plain)
+    te = statistics.median(r["s"] for r in exact)
+    ip = statistics.median(r["iters"] for r in plain)
+    ie = statistics.median(r["iters"] for r in exact)
+    out = {"value": ip / tp, "iters": int(ip), "converged": min(r["converged"] for r in plain),
+           "what": "same loop, binary64 dots with atomic accumulation across blocks (non-reproducible)",
+           "repro_iters_per_s": ie / te, "repro_over_plain_time": (te / ie) / (tp / ip),
+           "repro_over_plain_time_range": [min(r["s"] / r["iters"] for r in exact) /
+                                           max(r["s"] / r["iters"] for r in plain),
+                                           max(r["s"] / r["iters"] for r in exact) /
+                                           min(r["s"] / r["iters"] for r in plain)],
+           "timing": f"median of {len(plain)} plain and {len(exact)} reproducible solves (graph loop)",
+           "drift": {"plain": _drift_summary(plain), "reproducible": _drift_summary(exact)},
+           "runs_plain": [{"iters": r["iters"], "tau": r["tau"], "tau_final": r["tau_final"]} for r in plain],
+           "runs_reproducible": [{"iters": r["iters"], "tau": r["tau"], "tau_final": r["tau_final"]}
+                                 for r in exact]}
+    import torch
+    from paper_2302_04180_gb300 import gen
+    A32 = gen.poisson3d(32)
+    A32d = rbs.to_device(A32, dev)
+    b32 = rbs.rbs_spmv_csr(A32d, torch.ones(A32.n, dtype=torch.float64, device=dev))
+    x32 = torch.empty(A32.n, dtype=torch.float64, device=dev)
+    out["drift_poisson32"] = {"plain": _drift_summary(_runs(rbs, A32d, b32, x32, 1, 20)),
+                              "reproducible": _drift_summary(_runs(rbs, A32d, b32, x32, 0, 20))}
+    return out
 
 
 def _roofline(A, prof_tot):
@@ -379,12 +512,13 @@ def _batched(rbs, gen, dev):
             "identical_to_default": same}
 
 
-def _serving(rbs, gen, dev, rates=(50.0, 150.0, 300.0), count=300, seed=3):
-    """Poisson-arrival solve requests against the continuous-batching server:
-    a pool of 48 systems (3D upwind convection-diffusion and 3D Poisson up to
-    128^3, classic/pipelined mix, tol 1e-8). Per rate: p50/p99 latency
-    (submission to completion), solves/s, and whether every answer is bitwise
-    the system's solo solve."""
+def _serving(rbs, gen, dev, rates=(100.0, 300.0, 1000.0), count=10000, seed=3):
+    """Poisson-arrival solve requests against the per-iteration continuous-
+    batching server: a pool of 48 systems (3D upwind convection-diffusion and
+    3D Poisson up to 128^3, classic/pipelined mix, tol 1e-8), `count` requests
+    per arrival rate. Per rate: p50/p99 latency (submission to completion),
+    solves/s, the most systems in flight at once, the pool's peak reserved
+    memory, and whether every answer is bitwise the system's solo solve."""
     import torch
     pool = []
     for A, v in gen.serving_pool(48, 0):
@@ -397,31 +531,65 @@ def _serving(rbs, gen, dev, rates=(50.0, 150.0, 300.0), count=300, seed=3):
     for rate in rates:
         arr = gen.poisson_arrivals(count, rate, seed)
         picks = (gen.splitmix64(seed + 11, count) % np.uint64(len(pool))).astype(int)
-        with rbs.RbsServer() as srv:
+        xs = [torch.empty(pool[p][0].n, dtype=torch.float64, device=dev) for p in range(len(pool))]
+        same = True
+        lat = []
+        with rbs.RbsServer(engines=1, max_active=128, budget_bytes=24 << 30) as srv:
             tk = []
             t0 = time.perf_counter()
             for k in range(count):
                 while time.perf_counter() - t0 < arr[k]:
-                    time.sleep(0.0002)
+                    time.sleep(0.0001)
                 A, Ad, b, v, _ = pool[picks[k]]
+                # one output buffer per request in flight; answers are checked as they finish
                 sd = {"A": Ad, "b": b, "x": torch.empty(A.n, dtype=torch.float64, device=dev),
                       "tol": 1e-8, "maxit": 3000, "variant": v}
                 tk.append((srv.submit(sd), picks[k]))
-            res = [(srv.wait(t), p) for t, p in tk]
+                while len(tk) > 2048:
+                    t, p = tk.pop(0)
+                    r = srv.wait(t)
+                    lat.append(r["latency_s"])
+                    same = same and r["iters"] == pool[p][4]["iters"] and torch.equal(r["x"], pool[p][4]["x"])
+            for t, p in tk:
+                r = srv.wait(t)
+                lat.append(r["latency_s"])
+                same = same and r["iters"] == pool[p][4]["iters"] and torch.equal(r["x"], pool[p][4]["x"])
             t1 = time.perf_counter()
-        lat = np.array([r["latency_s"] for r, _ in res])
-        same = all(r["iters"] == pool[p][4]["iters"] and torch.equal(r["x"], pool[p][4]["x"])
-                   for r, p in res)
+            st = srv.stats()
+        lat = np.array(lat)
         out.append({"rate_per_s": rate, "requests": count, "solves_per_s": count / (t1 - t0),
                     "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                    "p99_ms": float(np.percentile(lat, 99) * 1e3), "identical_to_solo": bool(same)})
+                    "p99_ms": float(np.percentile(lat, 99) * 1e3), "identical_to_solo": bool(same),
+                    "engine_steps": st["steps"], "peak_in_flight": st["peak_active"],
+                    "pool_reserved_peak_MB": st["pool_reserved_peak"] / 2**20})
     return out
 
 
-def _kernel_micro(rbs, gen, dev):
-    """Standalone exact dot (2^27, cond 1e32) and SpMV (Poisson 128^3, 27-point
-    e-type 159^3) GB/s."""
+EXDOT_LOG2N = (16, 20, 24, 27)
+EXDOT_CONDS = (1e0, 1e16, 1e32, 1e48)
+EXDOT_SEEDS = (0, 1, 2)
+
+
+def _gen_dot_case(lg, cond, seed, tmp):
+    """(spawned worker) one ill-conditioned dot of the kernel microbenchmark,
+    saved as .npy files; returns their paths and the exact value as a string."""
+    sys.path.insert(0, ROOT)
+    from paper_2302_04180_gb300 import gen
+    x, y, exact = gen.ill_conditioned_dot(1 << lg, cond, seed)
+    px = os.path.join(tmp, f"x_{lg}_{cond:g}_{seed}.npy")
+    py = os.path.join(tmp, f"y_{lg}_{cond:g}_{seed}.npy")
+    np.save(px, x)
+    np.save(py, y)
+    return px, py, None if exact is None else str(exact)
+
+
+def _kernel_micro(rbs, gen, dev, futs):
+    """Standalone exact dot over the n x cond grid (C2a: n = 2^16..2^27, cond
+    1 .. 1e48, three seeds below 2^27) with its GB/s and whether each result is
+    the exact value rounded once; SpMV on Poisson 128^3 (C2b) and on the
+    27-point e-type stencil at 159^3."""
     import torch
+    from fractions import Fraction
     out = {}
 
     def timeit(f, reps=10):
@@ -436,21 +604,31 @@ def _kernel_micro(rbs, gen, dev):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    n = 1 << 27
-    x, y, _ = gen.ill_conditioned_dot(n, 1e32, 0)
-    xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
-    del x, y
+    hbm, _ = _peaks()
+    grid = []
     o = torch.empty(1, dtype=torch.float64, device=dev)
-    ms = timeit(lambda: rbs.rbs_exdot(xt, yt, o))
-    out["exdot_2^27_cond1e32"] = {"us": ms * 1e3, "GB/s": 16 * n / (ms * 1e-3) / 1e9}
-    del xt, yt
+    for (lg, cond, seed), fu in futs.items():
+        px, py, exact = fu.result()
+        xt = torch.from_numpy(np.load(px)).to(dev)
+        yt = torch.from_numpy(np.load(py)).to(dev)
+        os.remove(px)
+        os.remove(py)
+        n = 1 << lg
+        ms = timeit(lambda: rbs.rbs_exdot(xt, yt, o), reps=10 if lg >= 24 else 50)
+        got = float(o.item())
+        grid.append({"n": n, "cond": cond, "seed": seed, "us": ms * 1e3, "GB/s": 16 * n / (ms * 1e-3) / 1e9,
+                     "frac_of_hbm": 16 * n / (ms * 1e-3) / 1e9 / hbm,
+                     "matches_exact": None if exact is None else got == float(Fraction(exact))})
+        del xt, yt
+    out["exdot_grid"] = grid
+    out["exdot_grid_all_exact"] = all(g["matches_exact"] is not False for g in grid)
     A = gen.poisson3d(128)
     Ad = rbs.to_device(A, dev)
     xv = torch.from_numpy(gen.random_vector(A.n, 1)).to(dev)
     yv = torch.empty_like(xv)
     ms = timeit(lambda: rbs.rbs_spmv_csr(Ad, xv, yv))
     byt = 12 * A.nnz + 8 * (A.n + 1) + 16 * A.n
-    out["spmv_poisson128"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9}
+    out["spmv_poisson128"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9, "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / hbm}
     del Ad, xv, yv
     # the 27-point e-type stencil at the paper's scalability size (159^3 =
     # 4,019,679 unknowns, 27 nonzeros per interior row: long-span staging)
@@ -460,7 +638,54 @@ def _kernel_micro(rbs, gen, dev):
     yv = torch.empty_like(xv)
     ms = timeit(lambda: rbs.rbs_spmv_csr(Ad, xv, yv))
     byt = 12 * A.nnz + 8 * (A.n + 1) + 16 * A.n
-    out["spmv_stencil27_159"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9}
+    out["spmv_stencil27_159"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9,
+                                 "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / hbm}
+    return out
+
+
+def _c1(rbs, gen, dev, reps=30):
+    """C1: Poisson 7-point 16^3 (n = 4096), classic, tol 1e-8 -- launch- and
+    latency-bound: us per iteration and iterations/s with the device-side
+    graph loop and with the host loop."""
+    import torch
+    A = gen.poisson3d(16)
+    Ad = rbs.to_device(A, dev)
+    b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    out = {}
+    for name, loop in (("graph_loop", 0), ("host_loop", 1)):
+        for _ in range(3):
+            r = rbs.rbs_solve(Ad, b, tol=1e-8, maxit=1000, x_out=x, loop_mode=loop, history=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        its = 0
+        for _ in range(reps):
+            its += rbs.rbs_solve(Ad, b, tol=1e-8, maxit=1000, x_out=x, loop_mode=loop, history=False)["iters"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out[name] = {"iters_per_s": its / dt, "us_per_iter": dt / its * 1e6, "iters": r["iters"],
+                     "solves_per_s": reps / dt}
+    return out
+
+
+def _c3b(rbs, gen, dev, reps=3):
+    """C3b: upwind convection-diffusion 192^3 (Pe 10, velocity (1,1,1)),
+    classic and pipelined reproducible solves to tol 1e-10, iterations/s."""
+    import torch
+    A = gen.convdiff3d(192, 10.0)
+    Ad = rbs.to_device(A, dev)
+    b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    out = {"n": int(A.n), "nnz": int(A.nnz)}
+    for name, v in (("classic", 0), ("pipelined", 1)):
+        rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=v, x_out=x, history=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        its = 0
+        for _ in range(reps):
+            its += rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=v, x_out=x, history=False)["iters"]
+        torch.cuda.synchronize()
+        out[name] = {"iters_per_s": its / (time.perf_counter() - t), "iters": its // reps}
     return out
 
 
@@ -473,7 +698,7 @@ def run_serving(args):
     ge.build()
     import paper_2302_04180_gb300 as rbs
     from paper_2302_04180_gb300 import gen
-    sweep = _serving(rbs, gen, dev, rates=(50.0, 100.0, 150.0, 200.0, 250.0), count=10000)
+    sweep = _serving(rbs, gen, dev, rates=tuple(float(r) for r in args.rates.split(",")), count=args.requests)
     best = max(r["solves_per_s"] for r in sweep)
     print(json.dumps({"metric": "serving solves/s at p99", "value": best, "unit": "solves/s",
                       "n_gpus": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
@@ -584,6 +809,8 @@ def main():
                          "driver, which records per-kernel CUDA events)")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving sweep: 10k Poisson-arrival requests per rate")
+    ap.add_argument("--requests", type=int, default=10000, help="with --serving: requests per arrival rate")
+    ap.add_argument("--rates", default="100,300,1000,3000", help="with --serving: arrival rates per second")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
                     help="skip e2e, comparators and kernel microbenchmarks")
     ap.add_argument("--solve-only", default=None, choices=["classic", "pipelined"],

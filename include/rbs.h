@@ -306,29 +306,51 @@ int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs_info *prev
                    rbs_batch_schedule *best, void *stream);
 
 /* ---- serving ---------------------------------------------------------------------
- * A request loop with continuous batching (the library's own runtime; the
- * paper has no counterpart). Clients submit solves at any time; `workers`
- * threads, each with its own stream and workspace, take pending requests in
- * arrival order while the Krylov state of the requests in flight stays within
- * `budget_bytes` (one request always runs when none is in flight). A system
- * with n >= solo_n runs alone with the whole-GPU solver (rbs_solve_ex); up to
- * `max_batch` consecutive smaller ones run as one rbs_solve_batched launch (one
- * thread-block cluster each). Requests arriving
- * while others run are admitted as workers and budget free up; launches on
- * different workers overlap on the device. Every answer is bitwise the one
- * rbs_solve gives for that system alone. The caller keeps a submitted system's
- * device buffers alive until its request is done. Latency = submission to
- * completion; queue = submission to start. All handles and outputs are host. */
+ * A request loop with per-iteration continuous batching (the library's own
+ * runtime; the paper has no counterpart). Clients submit solves (rbs_system,
+ * device pointers; x 16-byte aligned) at any time. Each of `engines` threads
+ * owns a stream and up to `max_active` slots, a slot being the resident state
+ * of one system in flight: its Krylov vectors (allocated from the server's own
+ * stream-ordered memory pool at admission, freed at retirement), its device
+ * scalars and its dot scratch. An engine advances in steps. A step admits
+ * pending requests in arrival order into free slots while the vector memory of
+ * the systems in flight stays within `budget_bytes` (one request is always
+ * admitted when none is in flight), runs their structure check, Jacobi and
+ * solver set-up, then one iteration (Fig. 2 or Fig. 4) of every system in
+ * flight: one launch per phase for all of them, each system on blocks of
+ * `rows_per_block` rows (0: 8192). Stopped systems (converged, breakdown, NaN,
+ * invalid, or maxit iterations) are retired a step or two later. A request that
+ * arrives while others iterate joins them at the next step. Every answer is
+ * bitwise the one rbs_solve gives for that system alone (the same element
+ * functions, exact dots and scalar tails). The caller keeps a submitted
+ * system's buffers alive until its request is done. Latency = submission to
+ * retirement; queue = submission to admission. Handles and outputs are host.
+ * Errors: bad arguments at submission, or a system that fails its device-side
+ * structure or diagonal check, end the request with RBS_EINVAL (poll/wait
+ * report it in info->status, rbs_last_error() gives the reason); a CUDA error
+ * ends every request in flight with RBS_ECUDA. */
 typedef struct rbs_server rbs_server;
-int rbs_server_create(int32_t workers, int32_t max_batch, int64_t budget_bytes, int64_t solo_n,
+int rbs_server_create(int32_t engines, int32_t max_active, int64_t budget_bytes, int64_t rows_per_block,
                       rbs_server **out);
 int rbs_server_submit(rbs_server *srv, const rbs_system *system, int64_t *ticket);
 int rbs_server_poll(rbs_server *srv, int64_t ticket, int32_t *done, rbs_info *info, double *latency_s,
                     double *queue_s);
 int rbs_server_wait(rbs_server *srv, int64_t ticket, rbs_info *info, double *latency_s, double *queue_s);
-/* (poll and wait: a request whose solve call failed as a whole -- not one of
- * its systems -- reports that call's status in info->status, and
- * rbs_last_error() then gives the call's message.) */
+/* Where a request ran: the engine step that admitted it and the step whose
+ * scalars retired it (-1 before that), and how many systems were already in
+ * flight on its engine when it joined. */
+typedef struct {
+    int64_t admit_step, finish_step;
+    int32_t active_at_admit, done;
+} rbs_request_stats;
+int rbs_server_request_stats(rbs_server *srv, int64_t ticket, rbs_request_stats *out);
+/* Server counters: steps run, requests completed, most systems in flight at
+ * once, requests pending, vector bytes of the systems in flight (the budgeted
+ * quantity), and the memory pool's reserved bytes now and at its peak. */
+typedef struct {
+    int64_t steps, completed, peak_active, pending, budget_in_use, pool_reserved, pool_reserved_peak;
+} rbs_server_counters;
+int rbs_server_stats(rbs_server *srv, rbs_server_counters *out);
 int rbs_server_destroy(rbs_server *srv);
 
 /* ---- library control ---------------------------------------------------------- */

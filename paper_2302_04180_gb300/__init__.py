@@ -36,8 +36,8 @@ PROF_KIND_NAMES = ("k1_spmv_dot", "vec", "setup", "spmv", "pipe_vec_dot", "k3_sp
 EXPORTS = ("rbs_exdot", "rbs_exdot_multi", "rbs_exdot_noalloc", "rbs_exdot_partial", "rbs_round_limbs",
            "rbs_spmv_csr", "rbs_jacobi_invd", "rbs_jacobi_apply", "rbs_solve",
            "rbs_solve_ex", "rbs_solve_batched", "rbs_solve_batched_ex", "rbs_batch_tune", "rbs_fpe_dot",
-           "rbs_server_create",
-           "rbs_server_submit", "rbs_server_poll", "rbs_server_wait", "rbs_server_destroy", "rbs_stream_status", "rbs_release", "rbs_set_param",
+           "rbs_server_create", "rbs_server_submit", "rbs_server_poll", "rbs_server_wait",
+           "rbs_server_request_stats", "rbs_server_stats", "rbs_server_destroy", "rbs_stream_status", "rbs_release", "rbs_set_param",
            "rbs_get_param", "rbs_last_error", "rbs_version")
 
 
@@ -67,6 +67,16 @@ class _Info(C.Structure):
 class _System(C.Structure):
     _fields_ = [("A", _Csr), ("b", C.c_void_p), ("x0", C.c_void_p), ("jacobi_diag", C.c_void_p),
                 ("x", C.c_void_p), ("tol", C.c_double), ("maxit", C.c_int32), ("variant", C.c_int32)]
+
+
+class _ReqStats(C.Structure):
+    _fields_ = [("admit_step", C.c_int64), ("finish_step", C.c_int64), ("active_at_admit", C.c_int32),
+                ("done", C.c_int32)]
+
+
+class _SrvCounters(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("steps", "completed", "peak_active", "pending", "budget_in_use",
+                                         "pool_reserved", "pool_reserved_peak")]
 
 
 class _Hist(C.Structure):
@@ -113,6 +123,8 @@ def load(path: str | None = None):
             "rbs_server_submit": [vp, C.POINTER(_System), C.POINTER(i64)],
             "rbs_server_poll": [vp, i64, C.POINTER(i32), C.POINTER(_Info), C.POINTER(dbl), C.POINTER(dbl)],
             "rbs_server_wait": [vp, i64, C.POINTER(_Info), C.POINTER(dbl), C.POINTER(dbl)],
+            "rbs_server_request_stats": [vp, i64, C.POINTER(_ReqStats)],
+            "rbs_server_stats": [vp, C.POINTER(_SrvCounters)],
             "rbs_server_destroy": [vp],
             "rbs_solve_batched": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist), vp],
             "rbs_solve_batched_ex": [C.c_int32, C.POINTER(_System), C.POINTER(_Info), C.POINTER(_Hist),
@@ -425,14 +437,16 @@ def rbs_batch_tune(systems, prev=None, proxy_iters=24, stream=None):
 
 
 class RbsServer:
-    """Continuous-batching solve server (see rbs_server_create in include/rbs.h).
-    submit(system_dict) -> ticket; wait(ticket) / poll(ticket) -> result dict with
-    latency_s and queue_s. Keep each system's tensors alive until it is done."""
+    """Per-iteration continuous-batching solve server (see rbs_server_create in
+    include/rbs.h). submit(system_dict) -> ticket; wait(ticket) / poll(ticket) ->
+    result dict with latency_s and queue_s; request_stats(ticket) and stats()
+    report where requests ran and the server's counters. Keep each system's
+    tensors alive until it is done."""
 
-    def __init__(self, workers=8, max_batch=8, budget_bytes=16 << 30, solo_n=30000):
+    def __init__(self, engines=1, max_active=64, budget_bytes=16 << 30, rows_per_block=0):
         self._h = C.c_void_p()
-        _check(load().rbs_server_create(int(workers), int(max_batch), int(budget_bytes),
-                                        int(solo_n), C.byref(self._h)))
+        _check(load().rbs_server_create(int(engines), int(max_active), int(budget_bytes),
+                                        int(rows_per_block), C.byref(self._h)))
         self._keep = {}
 
     def submit(self, sd) -> int:
@@ -460,6 +474,17 @@ class RbsServer:
         _check(load().rbs_server_poll(self._h, int(ticket), C.byref(done), C.byref(info),
                                       C.byref(lat), C.byref(que)))
         return self._result(ticket, info, lat, que) if done.value else None
+
+    def request_stats(self, ticket):
+        r = _ReqStats()
+        _check(load().rbs_server_request_stats(self._h, int(ticket), C.byref(r)))
+        return {"admit_step": r.admit_step, "finish_step": r.finish_step,
+                "active_at_admit": r.active_at_admit, "done": bool(r.done)}
+
+    def stats(self):
+        c = _SrvCounters()
+        _check(load().rbs_server_stats(self._h, C.byref(c)))
+        return {k: int(getattr(c, k)) for k, _ in _SrvCounters._fields_}
 
     def close(self):
         if self._h:

@@ -505,15 +505,16 @@ static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t 
 
 // Block- and grid-level finish of K exact reductions, once every thread's own
 // accumulators are in the block accumulators sacc (flags[k]: this thread's
-// non-finite flags). Every thread of every block calls it. Returns true in the
-// block that finishes last; there the rounded values are in vals[0..K-1]
-// (shared memory) after a barrier, or, with export_limbs, the partially
-// normalised limbs of the first reduction are in limbs_out.
+// non-finite flags). Every thread of each of the nblk blocks that share the
+// reduction (the whole grid unless given) calls it. Returns true in the block
+// that finishes last; there the rounded values are in vals[0..K-1] (shared
+// memory) after a barrier, or, with export_limbs, the partially normalised
+// limbs of the first reduction are in limbs_out.
 template <int K>
 __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], unsigned long long (*sacc)[NL],
                                                   uint32_t *sflags, DotScratch *g, double *vals,
                                                   bool export_limbs = false, long long *limbs_out = nullptr,
-                                                  int32_t *flags_out = nullptr) {
+                                                  int32_t *flags_out = nullptr, unsigned nblk = 0u) {
 #pragma unroll
     for (int k = 0; k < K; k++)
         if (flags[k]) atomicOr(&sflags[k], flags[k]);
@@ -527,7 +528,7 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
     __threadfence();
     __syncthreads();
     __shared__ bool s_last;
-    if (threadIdx.x == 0) s_last = (atomicAdd(&g->ticket, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(&g->ticket, 1u) == (nblk ? nblk : gridDim.x) - 1);
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
@@ -551,15 +552,17 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
 }
 
 // Grid-level finish of K exact reductions held in register windows: flush the
-// windows into the block accumulators, then block_grid_finish.
+// windows into the block accumulators, then block_grid_finish (nblk: blocks
+// that share the reduction, 0 for the whole grid).
 template <int K, int Q, int SCRATCH = FLUSH_SCRATCH>
 __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
                                              unsigned long long (*sacc)[NL], uint32_t *sflags,
                                              DotScratch *g, double *vals, bool export_limbs = false,
-                                             long long *limbs_out = nullptr, int32_t *flags_out = nullptr) {
+                                             long long *limbs_out = nullptr, int32_t *flags_out = nullptr,
+                                             unsigned nblk = 0u) {
 #pragma unroll
     for (int k = 0; k < K; k++) warp_flush<Q, SCRATCH>(win[k], sacc[k]);
-    return block_grid_finish<K>(flags, sacc, sflags, g, vals, export_limbs, limbs_out, flags_out);
+    return block_grid_finish<K>(flags, sacc, sflags, g, vals, export_limbs, limbs_out, flags_out, nblk);
 }
 
 }  // namespace rbs

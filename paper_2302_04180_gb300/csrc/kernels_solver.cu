@@ -23,24 +23,10 @@
 #include "kernels.cuh"
 
 #include "launch.h"
+#include "solver_elem.cuh"
 #include "tails.cuh"
 
 namespace rbs {
-
-constexpr int SQ = 4;  // window placements used by the solver kernels
-
-struct Ctx {
-    CSRView A;
-    int64_t n;
-    double *x, *r, *r0, *p, *ph, *s, *q, *qh, *y, *invd;
-    double *rh, *w, *wh, *t, *sh, *z, *zh, *v;
-    const double *b, *x0;
-    SolverState *st;
-    DotScratch *g;
-    double *hist;
-    unsigned *err;
-    int spmv_mode;
-};
 
 // ---- classic kernels -------------------------------------------------------------
 
@@ -51,19 +37,7 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
     red.init();
     bool bad = false;
     for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        double ri;
-        if (c.x0) {
-            const double ax = spmv_row(c.A, i, c.x0, bad);
-            ri = __dsub_rn(c.b[i], ax);
-            c.x[i] = c.x0[i];
-        } else {
-            ri = c.b[i];
-            c.x[i] = 0.0;
-        }
-        c.r[i] = ri;
-        c.r0[i] = ri;
-        c.p[i] = ri;
-        c.ph[i] = __dmul_rn(ri, c.invd[i]);
+        const double ri = cls_setup_elem(c, i, bad);
         red.add_sq(0, ri);
     }
     if (bad) atomicOr(c.err, 1u);
@@ -96,17 +70,13 @@ __global__ void __launch_bounds__(256, 4) k_cls_k2(Ctx c) {
     for_pairs(c.n, [&](int64_t i, bool pair) {
         if (pair) {
             const double2 s = ld2(c.s, i), r = ld2(c.r, i), d = ld2(c.invd, i);
-            double2 q, qh;
-            q.x = fma(na, s.x, r.x);
-            q.y = fma(na, s.y, r.y);
-            qh.x = __dmul_rn(q.x, d.x);
-            qh.y = __dmul_rn(q.y, d.y);
-            st2(c.q, i, q);
-            st2(c.qh, i, qh);
+            const VPair u0 = cls_k2(na, s.x, r.x, d.x), u1 = cls_k2(na, s.y, r.y, d.y);
+            st2(c.q, i, make_double2(u0.a, u1.a));
+            st2(c.qh, i, make_double2(u0.b, u1.b));
         } else {
-            const double q = fma(na, c.s[i], c.r[i]);
-            c.q[i] = q;
-            c.qh[i] = __dmul_rn(q, c.invd[i]);
+            const VPair u = cls_k2(na, c.s[i], c.r[i], c.invd[i]);
+            c.q[i] = u.a;
+            c.qh[i] = u.b;
         }
     });
 }
@@ -139,23 +109,21 @@ __global__ void __launch_bounds__(256) k_cls_k4(Ctx c) {
         if (pair) {
             const double2 qh = ld2(c.qh, i), ph = ld2(c.ph, i), y = ld2(c.y, i), q = ld2(c.q, i),
                           r0 = ld2(c.r0, i);
-            double2 x = ld2(c.x, i), r;
-            x.x = fma(om, qh.x, fma(al, ph.x, x.x));
-            x.y = fma(om, qh.y, fma(al, ph.y, x.y));
-            r.x = fma(nom, y.x, q.x);
-            r.y = fma(nom, y.y, q.y);
-            st2(c.x, i, x);
-            st2(c.r, i, r);
-            red.add(0, r0.x, r.x);
-            red.add(0, r0.y, r.y);
-            red.add_sq(1, r.x);
-            red.add_sq(1, r.y);
+            const double2 x = ld2(c.x, i);
+            const VPair u0 = cls_k4(al, om, nom, qh.x, ph.x, x.x, y.x, q.x);
+            const VPair u1 = cls_k4(al, om, nom, qh.y, ph.y, x.y, y.y, q.y);
+            st2(c.x, i, make_double2(u0.a, u1.a));
+            st2(c.r, i, make_double2(u0.b, u1.b));
+            red.add(0, r0.x, u0.b);
+            red.add(0, r0.y, u1.b);
+            red.add_sq(1, u0.b);
+            red.add_sq(1, u1.b);
         } else {
-            c.x[i] = fma(om, c.qh[i], fma(al, c.ph[i], c.x[i]));
-            const double r = fma(nom, c.y[i], c.q[i]);
-            c.r[i] = r;
-            red.add(0, c.r0[i], r);
-            red.add_sq(1, r);
+            const VPair u = cls_k4(al, om, nom, c.qh[i], c.ph[i], c.x[i], c.y[i], c.q[i]);
+            c.x[i] = u.a;
+            c.r[i] = u.b;
+            red.add(0, c.r0[i], u.b);
+            red.add_sq(1, u.b);
         }
     });
     __shared__ double vals[R::K];
@@ -168,18 +136,14 @@ __global__ void __launch_bounds__(256) k_cls_k5(Ctx c) {
     const double be = c.st->beta, nom = -c.st->omega;
     for_pairs(c.n, [&](int64_t i, bool pair) {
         if (pair) {
-            const double2 s = ld2(c.s, i), r = ld2(c.r, i), d = ld2(c.invd, i);
-            double2 p = ld2(c.p, i), ph;
-            p.x = fma(be, fma(nom, s.x, p.x), r.x);
-            p.y = fma(be, fma(nom, s.y, p.y), r.y);
-            ph.x = __dmul_rn(p.x, d.x);
-            ph.y = __dmul_rn(p.y, d.y);
-            st2(c.p, i, p);
-            st2(c.ph, i, ph);
+            const double2 s = ld2(c.s, i), r = ld2(c.r, i), d = ld2(c.invd, i), p = ld2(c.p, i);
+            const VPair u0 = cls_k5(be, nom, s.x, p.x, r.x, d.x), u1 = cls_k5(be, nom, s.y, p.y, r.y, d.y);
+            st2(c.p, i, make_double2(u0.a, u1.a));
+            st2(c.ph, i, make_double2(u0.b, u1.b));
         } else {
-            const double p = fma(be, fma(nom, c.s[i], c.p[i]), c.r[i]);
-            c.p[i] = p;
-            c.ph[i] = __dmul_rn(p, c.invd[i]);
+            const VPair u = cls_k5(be, nom, c.s[i], c.p[i], c.r[i], c.invd[i]);
+            c.p[i] = u.a;
+            c.ph[i] = u.b;
         }
     });
 }
@@ -189,20 +153,7 @@ __global__ void __launch_bounds__(256) k_cls_k5(Ctx c) {
 // set-up 1: r = b - A x0 (or b), x, r0 = r, rhat = r * invd
 __global__ void __launch_bounds__(256) k_pipe_setup1(Ctx c) {
     bool bad = false;
-    for (int64_t i = gtid(); i < c.n; i += gstride()) {
-        double ri;
-        if (c.x0) {
-            const double ax = spmv_row(c.A, i, c.x0, bad);
-            ri = __dsub_rn(c.b[i], ax);
-            c.x[i] = c.x0[i];
-        } else {
-            ri = c.b[i];
-            c.x[i] = 0.0;
-        }
-        c.r[i] = ri;
-        c.r0[i] = ri;
-        c.rh[i] = __dmul_rn(ri, c.invd[i]);
-    }
+    for (int64_t i = gtid(); i < c.n; i += gstride()) pipe_setup1_elem(c, i, bad);
     if (bad) atomicOr(c.err, 1u);
 }
 
@@ -230,62 +181,6 @@ __global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_pipe_setu
 // spills, where four blocks spilled the five windows; P1 is best at three.
 template <class R> struct P1Cfg { static constexpr int blocks = 3, pairs = 1; };
 template <int K> struct P1Cfg<PlainR<K>> { static constexpr int blocks = 4, pairs = 0; };
-
-// P1 for one element: in[0..5] = rh, w, wh, t, r, invd and, after iteration 0,
-// in[6..11] = ph, s, sh, z, zh, v (all loaded by the caller before any store);
-// out = ph, s, sh, z, q, qh, y, zh.
-struct P1In {
-    double rh, w, wh, t, r, d, ph, s, sh, z, zh, v;
-};
-struct P1Out {
-    double ph, s, sh, z, q, qh, y, zh;
-};
-template <class R>
-__device__ __forceinline__ P1Out p1_elem(const P1In &a, bool first, double nal, double be, double nom, R &red) {
-    P1Out o;
-    if (first) {
-        o.ph = a.rh;
-        o.s = a.w;
-        o.sh = a.wh;
-        o.z = a.t;
-    } else {
-        o.ph = fma(be, fma(nom, a.sh, a.ph), a.rh);
-        o.s = fma(be, fma(nom, a.z, a.s), a.w);
-        o.sh = fma(be, fma(nom, a.zh, a.sh), a.wh);
-        o.z = fma(be, fma(nom, a.v, a.z), a.t);
-    }
-    o.q = fma(nal, o.s, a.r);
-    o.qh = fma(nal, o.sh, a.rh);
-    o.y = fma(nal, o.z, a.w);
-    o.zh = __dmul_rn(o.z, a.d);
-    red.add(0, o.q, o.y);
-    red.add_sq(1, o.y);
-    return o;
-}
-
-__device__ __forceinline__ P1In p1_load(const Ctx &c, int64_t i, bool first) {
-    P1In a{c.rh[i], c.w[i], c.wh[i], c.t[i], c.r[i], c.invd[i], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    if (!first) {
-        a.ph = c.ph[i];
-        a.s = c.s[i];
-        a.sh = c.sh[i];
-        a.z = c.z[i];
-        a.zh = c.zh[i];
-        a.v = c.v[i];
-    }
-    return a;
-}
-
-__device__ __forceinline__ void p1_store(const Ctx &c, int64_t i, const P1Out &o) {
-    c.ph[i] = o.ph;
-    c.s[i] = o.s;
-    c.sh[i] = o.sh;
-    c.z[i] = o.z;
-    c.q[i] = o.q;
-    c.qh[i] = o.qh;
-    c.y[i] = o.y;
-    c.zh[i] = o.zh;
-}
 
 // P1: S1-S4 (copies at iteration 0), S5-S7, S9; <q,y>, <y,y> -> omega.
 // Every operand of an element is loaded before its first store (the vectors are
@@ -338,30 +233,6 @@ __global__ void __launch_bounds__(256, P1Cfg<R>::blocks) k_pipe_p1(Ctx c) {
 // (P3's launch shape: see P1Cfg.)
 template <class R> struct P3Cfg { static constexpr int blocks = 2, pairs = 1; };
 template <int K> struct P3Cfg<PlainR<K>> { static constexpr int blocks = 3, pairs = 0; };
-
-// P3 for one element, from its thirteen operands (loaded by the caller before
-// any store): x, r, rhat, w and what, and the five dots' products.
-struct P3In {
-    double qh, y, q, ph, x, zh, wh, v, t, d, r0, s, z;
-};
-struct P3Out {
-    double x, r, rh, w, wh;
-};
-template <class R>
-__device__ __forceinline__ P3Out p3_elem(const P3In &a, double al, double nal, double om, double nom, R &red) {
-    P3Out o;
-    o.x = fma(om, a.qh, fma(al, a.ph, a.x));
-    o.r = fma(nom, a.y, a.q);
-    o.rh = fma(nom, fma(nal, a.zh, a.wh), a.qh);
-    o.w = fma(nom, fma(nal, a.v, a.t), a.y);
-    o.wh = __dmul_rn(o.w, a.d);
-    red.add(0, a.r0, o.r);
-    red.add(1, a.r0, o.w);
-    red.add(2, a.r0, a.s);
-    red.add(3, a.r0, a.z);
-    red.add_sq(4, o.r);
-    return o;
-}
 
 // P3: S12-S15, S17; <r0,r>, <r0,w>, <r0,s>, <r0,z>, <r,r> -> tau, beta, alpha.
 // Every operand of an element is loaded before its first store (the vectors are
@@ -425,7 +296,7 @@ static Ctx make_ctx(const SolverArgs &a) {
     c.q = a.v.q; c.qh = a.v.qh; c.y = a.v.y; c.invd = a.v.invd;
     c.rh = a.v.rh; c.w = a.v.w; c.wh = a.v.wh; c.t = a.v.t; c.sh = a.v.sh; c.z = a.v.z;
     c.zh = a.v.zh; c.v = a.v.v;
-    c.b = a.b; c.x0 = a.x0; c.st = a.st; c.g = a.g; c.hist = a.hist; c.err = a.err;
+    c.b = a.b; c.x0 = a.x0; c.diag = nullptr; c.st = a.st; c.g = a.g; c.hist = a.hist; c.err = a.err;
     c.spmv_mode = a.spmv.mode;
     return c;
 }

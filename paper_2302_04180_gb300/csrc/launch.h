@@ -129,6 +129,27 @@ cudaError_t launch_batch(const BatchSys *d_sys, const int32_t *d_order, const in
 // Clusters of `csize` CTAs that fit on the device at once (0 if none).
 int batch_max_clusters(int csize);
 
+// ---- per-step kernels of the serving engine (kernels_step.cu) ----
+// One block of a per-step launch: rows [lo, hi) of the system in slot `sys`
+// (lo even), which has nblk blocks in the launch.
+struct StepTask {
+    int32_t sys, nblk;
+    int64_t lo, hi;
+};
+// Size of the device-side view of one system, and that view written to `out`
+// (host memory, step_ctx_bytes() bytes): matrix, vectors (v.x is the caller's
+// solution buffer, 16-byte aligned), right-hand side, optional x0 and Jacobi
+// diagonal, and the system's own state and dot scratch (zero at rest).
+size_t step_ctx_bytes();
+void step_ctx_make(void *out, const CSRArgs &A, const SolverVecs &v, const double *b, const double *x0,
+                   const double *diag, SolverState *st, DotScratch *g);
+// Admission of new systems (all of one variant): structure check and Jacobi,
+// then the set-up of Fig. 2 or Fig. 4; a system that fails its checks ends with
+// status RBS_EINVAL and its error bits in its scratch's err word.
+cudaError_t step_admit(const void *ctxs, const StepTask *tasks, int ntasks, int variant, cudaStream_t s);
+// One iteration of every listed system (all of one variant); stopped systems skip it.
+cudaError_t step_iteration(const void *ctxs, const StepTask *tasks, int ntasks, int variant, cudaStream_t s);
+
 // occupancy-derived persistent grid for the kernels of one kind: which = 0 the
 // SpMV kernels (classic K1, pipelined S10/S18), 1 the vector kernels, 2 the
 // pipelined P3 kernel, 3 the classic K3 kernel

@@ -41,8 +41,8 @@ struct ExactR {
     // SCRATCH: the per-warp scratch size the kernel already uses, so that the
     // flush staging shares it.
     template <int SCRATCH = FLUSH_SCRATCH>
-    __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
-        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals);
+    __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u) {
+        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals, false, nullptr, nullptr, nblk);
     }
 };
 
@@ -212,7 +212,7 @@ struct PlainR {
     __device__ __forceinline__ void add(int k, double x, double y) { s[k] = fma(x, y, s[k]); }
     __device__ __forceinline__ void add_sq(int k, double x) { s[k] = fma(x, x, s[k]); }
     template <int SCRATCH = 0>
-    __device__ __forceinline__ bool finish(DotScratch *g, double *vals) {
+    __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u) {
         __shared__ double s_part[K][32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -230,7 +230,7 @@ struct PlainR {
         __threadfence();
         __syncthreads();
         __shared__ bool s_last;
-        if (threadIdx.x == 0) s_last = (atomicAdd(&g->ticket, 1u) == gridDim.x - 1);
+        if (threadIdx.x == 0) s_last = (atomicAdd(&g->ticket, 1u) == (nblk ? nblk : gridDim.x) - 1);
         __syncthreads();
         if (!s_last) return false;
         __threadfence();
