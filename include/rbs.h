@@ -270,13 +270,17 @@ typedef struct {
 int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
                       void *stream);
 
-/* Schedule of a batched launch (the library's own tuning; the paper has
- * none). The launch is made of thread-block clusters of `cluster` CTAs (1, 2,
- * 4, 8 or 16; 16 needs the device's non-portable cluster size). Systems are
- * queued largest first; one with at least `split` unknowns is solved by a
- * whole cluster (rows split across its CTAs, dots reduced through distributed
- * shared memory), and from the first smaller one on every CTA takes systems
- * alone. `ms` is the tuner's measured time of its proxy run (0 otherwise).
+/* Schedule of a batched solve (the library's own tuning; the paper has
+ * none). cluster 1, 2, 4, 8 or 16: one persistent launch of thread-block
+ * clusters of `cluster` CTAs (16 needs the device's non-portable cluster
+ * size); systems are queued largest first, one with at least `split` unknowns
+ * is solved by a whole cluster (rows split across its CTAs, dots reduced
+ * through distributed shared memory), and from the first smaller one on every
+ * CTA takes systems alone. cluster 0, the stepped schedule: every system
+ * advances one iteration per step, one launch per phase of Fig. 2 / Fig. 4 for
+ * all of them, each system on blocks of `split` rows (0: 8192), so a large
+ * system spreads over as many SMs as its rows fill (x must be 16-byte
+ * aligned). `ms` is the tuner's measured time of its proxy run (0 otherwise).
  * Results never depend on the schedule: every system's iterates are bitwise
  * those of rbs_solve. */
 typedef struct {
@@ -295,8 +299,9 @@ int rbs_solve_batched_ex(int32_t nsys, const rbs_system *systems, rbs_info *info
 /* Autotune the batched schedule for this batch: times proxy solves of the
  * systems (each stopped after a number of iterations) under candidate
  * schedules -- every cluster size at the median split, then every split
- * candidate (system-size quantiles, 0 and "no cluster") at the best size --
- * and returns the fastest in *best, which later rbs_solve_batched calls on this
+ * candidate (system-size quantiles, 0 and "no cluster") at the best size, then
+ * the stepped schedule at 2048, 8192 and 32768 rows per block -- and returns
+ * the fastest in *best, which later rbs_solve_batched calls on this
  * device use. The proxy iteration cap of system i is proxy_iters, or, given a
  * previous solve's infos (`prev`, nsys entries, nullable), proxy_iters scaled
  * by prev[i].iters / max_j prev[j].iters so that systems keep their relative

@@ -109,6 +109,7 @@ struct Workspace {
     unsigned *h_err = nullptr;
     Buf vec, hist, stage[8];
     Buf batch_work, batch_hist, batch_sys, batch_order, batch_out, batch_queue;
+    Buf step_ctx, step_state, step_scr, step_tasks;  // the stepped batch schedule
     std::vector<cudaEvent_t> evpool;
     std::vector<cudaEvent_t> ev_chunk;
     // graph loop: one iteration captured as the body of a conditional WHILE node
@@ -174,7 +175,7 @@ void ws_free(Workspace *w) {
     cudaFree(w->vec.p);
     cudaFree(w->hist.p);
     for (Buf *b : {&w->batch_work, &w->batch_hist, &w->batch_sys, &w->batch_order, &w->batch_out,
-                   &w->batch_queue})
+                   &w->batch_queue, &w->step_ctx, &w->step_state, &w->step_scr, &w->step_tasks})
         cudaFree(b->p);
     for (auto &b : w->stage) cudaFree(b.p);
     for (auto e : w->evpool) cudaEventDestroy(e);
@@ -799,7 +800,190 @@ rbs_batch_schedule default_schedule() {
 }
 
 bool schedule_ok(const rbs_batch_schedule &s) {
-    return s.cluster >= 1 && s.cluster <= 16 && (s.cluster & (s.cluster - 1)) == 0 && s.split >= 0;
+    return s.cluster >= 0 && s.cluster <= 16 && (s.cluster & (s.cluster - 1)) == 0 && s.split >= 0;
+}
+
+// The stepped schedule (cluster 0): every system of the batch advances one
+// iteration per step, one launch per phase for all of them (the serving
+// engine's per-step kernels), each on blocks of `split` rows (0: 8192), so a
+// large system runs on as many SMs as its rows fill. The host enqueues steps in
+// chunks no longer than any system's remaining iterations (a system runs
+// exactly min(maxit, its own stop) iterations), reads every state after each
+// chunk and drops the stopped systems from the next chunk's task lists.
+// proxy_maxit / ms: as batch_solve.
+int batch_stepped(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
+                  const rbs_batch_schedule &sched, const int32_t *proxy_maxit, float *ms) {
+    const bool proxy = proxy_maxit != nullptr;
+    const int64_t rows = sched.split > 0 ? (sched.split + 63) / 64 * 64 : 8192;
+    std::vector<char> valid((size_t)nsys, 1);
+    std::vector<int32_t> maxit((size_t)nsys, 0);
+    size_t work_elems = 0, hist_recs = 0;
+    for (int i = 0; i < nsys; i++) {
+        const rbs_system &S = systems[i];
+        memset(&infos[i], 0, sizeof infos[i]);
+        bool ok = S.A.n > 0 && S.A.n <= 0x7fffffff && S.A.nnz >= 0 && S.A.rowptr &&
+                  (S.A.nnz == 0 || (S.A.col && S.A.val)) && S.b && (S.x || proxy) && S.maxit >= 0 &&
+                  S.tol >= 0.0 && (S.variant == RBS_CLASSIC || S.variant == RBS_PIPELINED);
+        ok = ok && is_device_ptr(S.A.rowptr) && is_device_ptr(S.b) && (proxy || is_device_ptr(S.x)) &&
+             (proxy || ((uintptr_t)S.x & 15) == 0) &&
+             (S.A.nnz == 0 || (is_device_ptr(S.A.col) && is_device_ptr(S.A.val))) &&
+             (!S.x0 || is_device_ptr(S.x0)) && (!S.jacobi_diag || is_device_ptr(S.jacobi_diag));
+        if (hists && (hists[i].cap < 0 || (hists[i].cap > 0 && !hists[i].rec))) ok = false;
+        valid[(size_t)i] = ok;
+        if (!ok) continue;
+        maxit[(size_t)i] = proxy ? std::min(S.maxit, std::max(proxy_maxit[i], 1)) : S.maxit;
+        const int64_t stride = (S.A.n + 31) / 32 * 32;
+        work_elems += (size_t)stride * ((S.variant == RBS_PIPELINED ? 16 : 9) + (proxy ? 1 : 0));
+        const int cap = hists ? std::min(hists[i].cap, S.maxit) : 0;
+        hist_recs += (size_t)(cap > 0 ? cap : 0);
+    }
+    const size_t cb = step_ctx_bytes();
+    CK(ensure(w->batch_work, work_elems * 8));
+    CK(ensure(w->batch_hist, (hist_recs > 0 ? hist_recs : 1) * RBS_HIST_W * 8));
+    CK(ensure(w->step_ctx, (size_t)nsys * cb));
+    CK(ensure(w->step_state, (size_t)nsys * sizeof(SolverState)));
+    CK(ensure(w->step_scr, (size_t)nsys * sizeof(DotScratch)));
+    std::vector<char> hctx((size_t)nsys * cb, 0);
+    std::vector<SolverState> hst((size_t)nsys);
+    std::vector<double *> hist_dev((size_t)nsys, nullptr);
+    std::vector<int32_t> hist_cap((size_t)nsys, 0);
+    SolverState *dst = (SolverState *)w->step_state.p;
+    DotScratch *dscr = (DotScratch *)w->step_scr.p;
+    size_t woff = 0, hoff = 0;
+    for (int i = 0; i < nsys; i++) {
+        SolverState &h = hst[(size_t)i];
+        memset(&h, 0, sizeof h);
+        if (!valid[(size_t)i]) {
+            h.done = 1;
+            h.status = RBS_EINVAL;
+            continue;
+        }
+        const rbs_system &S = systems[i];
+        const int64_t stride = (S.A.n + 31) / 32 * 32;
+        const int nv = S.variant == RBS_PIPELINED ? 16 : 9;
+        double *v[17];
+        for (int k = 0; k < nv; k++) v[k] = (double *)w->batch_work.p + woff + (size_t)k * stride;
+        woff += (size_t)stride * nv;
+        SolverVecs V;
+        memset(&V, 0, sizeof V);
+        V.x = S.x;
+        if (proxy) {
+            V.x = (double *)w->batch_work.p + woff;
+            woff += (size_t)stride;
+        }
+        V.r = v[0]; V.r0 = v[1]; V.ph = v[2]; V.s = v[3]; V.q = v[4]; V.qh = v[5]; V.y = v[6]; V.invd = v[7];
+        if (S.variant == RBS_CLASSIC) {
+            V.p = v[8];
+        } else {
+            V.rh = v[8]; V.w = v[9]; V.wh = v[10]; V.t = v[11]; V.sh = v[12]; V.z = v[13]; V.zh = v[14]; V.v = v[15];
+        }
+        const int cap = hists ? std::min(hists[i].cap, S.maxit) : 0;
+        hist_cap[(size_t)i] = cap > 0 ? cap : 0;
+        if (hist_cap[(size_t)i]) {
+            hist_dev[(size_t)i] = (double *)w->batch_hist.p + hoff * RBS_HIST_W;
+            hoff += (size_t)hist_cap[(size_t)i];
+        }
+        h.tol = S.tol;
+        h.maxit = maxit[(size_t)i];
+        h.variant = S.variant;
+        h.hist_cap = hist_cap[(size_t)i];
+        CSRArgs A{S.A.n, S.A.nnz, S.A.rowptr, S.A.col, S.A.val};
+        step_ctx_make(hctx.data() + (size_t)i * cb, A, V, S.b, S.x0, S.jacobi_diag, dst + i, dscr + i,
+                      hist_dev[(size_t)i]);
+    }
+    // tasks of a set of systems of one variant, appended to `out`
+    auto tasks_of = [&](const std::vector<int> &ids, std::vector<StepTask> &out) {
+        for (int i : ids) {
+            const int64_t n = systems[i].A.n;
+            const int nb = (int)((n + rows - 1) / rows);
+            for (int b = 0; b < nb; b++)
+                out.push_back(StepTask{i, nb, (int64_t)b * rows, std::min(n, (int64_t)(b + 1) * rows)});
+        }
+    };
+    std::vector<int> cls, pipe;
+    for (int i = 0; i < nsys; i++)
+        if (valid[(size_t)i]) (systems[i].variant == RBS_PIPELINED ? pipe : cls).push_back(i);
+    std::vector<StepTask> tasks;
+    tasks_of(cls, tasks);
+    const size_t ncls = tasks.size();
+    tasks_of(pipe, tasks);
+    CK(ensure(w->step_tasks, std::max<size_t>(tasks.size(), 1) * sizeof(StepTask)));
+    StepTask *dtask = (StepTask *)w->step_tasks.p;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, w->stream));
+    }
+    CK(cudaMemcpyAsync(w->step_ctx.p, hctx.data(), (size_t)nsys * cb, cudaMemcpyHostToDevice, w->stream));
+    CK(cudaMemcpyAsync(dst, hst.data(), (size_t)nsys * sizeof(SolverState), cudaMemcpyHostToDevice, w->stream));
+    CK(cudaMemsetAsync(dscr, 0, (size_t)nsys * sizeof(DotScratch), w->stream));
+    if (!tasks.empty())
+        CK(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(StepTask), cudaMemcpyHostToDevice, w->stream));
+    CK(step_admit(w->step_ctx.p, dtask, (int)ncls, RBS_CLASSIC, w->stream));
+    CK(step_admit(w->step_ctx.p, dtask + ncls, (int)(tasks.size() - ncls), RBS_PIPELINED, w->stream));
+    CK(cudaMemcpyAsync(hst.data(), dst, (size_t)nsys * sizeof(SolverState), cudaMemcpyDeviceToHost, w->stream));
+    CK(cudaStreamSynchronize(w->stream));
+    std::vector<int32_t> ran((size_t)nsys, 0);
+    auto live = [&](int i) { return !hst[(size_t)i].done && ran[(size_t)i] < maxit[(size_t)i]; };
+    for (;;) {
+        std::vector<int> c2, p2;
+        int32_t chunk = 8;
+        for (int i : cls)
+            if (live(i)) c2.push_back(i), chunk = std::min(chunk, maxit[(size_t)i] - ran[(size_t)i]);
+        for (int i : pipe)
+            if (live(i)) p2.push_back(i), chunk = std::min(chunk, maxit[(size_t)i] - ran[(size_t)i]);
+        if (c2.empty() && p2.empty()) break;
+        tasks.clear();
+        tasks_of(c2, tasks);
+        const size_t nc = tasks.size();
+        tasks_of(p2, tasks);
+        CK(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(StepTask), cudaMemcpyHostToDevice, w->stream));
+        for (int k = 0; k < chunk; k++) {
+            CK(step_iteration(w->step_ctx.p, dtask, (int)nc, RBS_CLASSIC, w->stream));
+            CK(step_iteration(w->step_ctx.p, dtask + nc, (int)(tasks.size() - nc), RBS_PIPELINED, w->stream));
+        }
+        for (int i : c2) ran[(size_t)i] += chunk;
+        for (int i : p2) ran[(size_t)i] += chunk;
+        // pageable host target: the copy returns once the data is there
+        CK(cudaMemcpyAsync(hst.data(), dst, (size_t)nsys * sizeof(SolverState), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaStreamSynchronize(w->stream));
+    }
+    if (ms) {
+        CK(cudaEventRecord(e1, w->stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    int ret = RBS_OK;
+    for (int i = 0; i < nsys; i++) {
+        rbs_info &I = infos[i];
+        const SolverState &q = hst[(size_t)i];
+        if (!valid[(size_t)i] || q.status == RBS_EINVAL) {
+            I.status = RBS_EINVAL;
+            ret = RBS_EINVAL;
+            if (hists) hists[i].len = 0;
+            continue;
+        }
+        I.iters = q.iter;
+        I.status = q.status;
+        I.converged = (q.status == RBS_OK && !(q.tau > q.tau_max)) ? 1 : 0;
+        I.tau0 = q.tau0;
+        I.tau_final = q.tau;
+        I.rho0 = q.rho0;
+        I.tau_max = q.tau_max;
+        I.alpha0 = systems[i].variant == RBS_PIPELINED ? q.alpha0 : __builtin_nan("");
+        I.mu0 = systems[i].variant == RBS_PIPELINED ? q.mu0 : 0.0;
+        if (hists) {
+            hists[i].len = std::min(q.iter, hist_cap[(size_t)i]);
+            if (hists[i].len > 0)
+                CK(cudaMemcpy(hists[i].rec, hist_dev[(size_t)i], (size_t)hists[i].len * RBS_HIST_W * 8,
+                              cudaMemcpyDeviceToHost));
+        }
+    }
+    if (ret) fail(ret, "one or more systems failed the argument or structure checks");
+    return ret;
 }
 
 // Solve the batch with schedule `sched`. With proxy_maxit (nsys entries) each
@@ -808,6 +992,7 @@ bool schedule_ok(const rbs_batch_schedule &s) {
 // device time of the prepare + solve launches.
 int batch_solve(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
                 const rbs_batch_schedule &sched, const int32_t *proxy_maxit, float *ms) {
+    if (sched.cluster == 0) return batch_stepped(w, nsys, systems, infos, hists, sched, proxy_maxit, ms);
     std::vector<BatchSys> sys((size_t)nsys);
     std::vector<char> valid((size_t)nsys, 1);
     size_t work_elems = 0, hist_recs = 0;
@@ -1047,7 +1232,7 @@ extern "C" int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs
         rbs_batch_schedule s = default_schedule();
         s.cluster = cluster;
         s.split = split;
-        if (batch_max_clusters(cluster) < 1) return RBS_OK;
+        if (cluster > 0 && batch_max_clusters(cluster) < 1) return RBS_OK;
         float ms = 0.f;
         int r = batch_solve(w, nsys, systems, infos.data(), nullptr, s, cap.data(), &ms);
         if (r && r != RBS_EINVAL) return r;
@@ -1064,6 +1249,9 @@ extern "C" int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs
     if (bestc > 1)
         for (size_t k = 0; k < splits.size(); k++)
             if (k != 1 && (rc = trial(bestc, splits[k]))) return rc;
+    // the stepped schedule (cluster 0) at three block sizes
+    for (int64_t rows : {2048, 8192, 32768})
+        if ((rc = trial(0, rows))) return rc;
     top.ms = top_ms;
     *best = top;
     std::lock_guard<std::mutex> lk2(g_tuned_mu);

@@ -316,7 +316,7 @@ void step_carveout() {
 }  // namespace
 
 void step_ctx_make(void *out, const CSRArgs &A, const SolverVecs &v, const double *b, const double *x0,
-                   const double *diag, SolverState *st, DotScratch *g) {
+                   const double *diag, SolverState *st, DotScratch *g, double *hist) {
     Ctx c;
     memset(&c, 0, sizeof c);
     c.A = CSRView{A.n, A.nnz, A.rowptr, A.col, A.val};
@@ -329,7 +329,7 @@ void step_ctx_make(void *out, const CSRArgs &A, const SolverVecs &v, const doubl
     c.diag = diag;
     c.st = st;
     c.g = g;
-    c.hist = nullptr;
+    c.hist = hist;
     c.err = &g->err;
     c.spmv_mode = SPMV_MODE_SHORT;
     memcpy(out, &c, sizeof c);

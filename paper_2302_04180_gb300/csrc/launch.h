@@ -139,10 +139,11 @@ struct StepTask {
 // Size of the device-side view of one system, and that view written to `out`
 // (host memory, step_ctx_bytes() bytes): matrix, vectors (v.x is the caller's
 // solution buffer, 16-byte aligned), right-hand side, optional x0 and Jacobi
-// diagonal, and the system's own state and dot scratch (zero at rest).
+// diagonal, the system's own state and dot scratch (zero at rest), and its
+// device history records (nullable; state->hist_cap of them).
 size_t step_ctx_bytes();
 void step_ctx_make(void *out, const CSRArgs &A, const SolverVecs &v, const double *b, const double *x0,
-                   const double *diag, SolverState *st, DotScratch *g);
+                   const double *diag, SolverState *st, DotScratch *g, double *hist);
 // Admission of new systems (all of one variant): structure check and Jacobi,
 // then the set-up of Fig. 2 or Fig. 4; a system that fails its checks ends with
 // status RBS_EINVAL and its error bits in its scratch's err word.

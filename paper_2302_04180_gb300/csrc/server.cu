@@ -261,7 +261,7 @@ void Server::engine_loop() {
                 V.rh = v[8]; V.w = v[9]; V.wh = v[10]; V.t = v[11]; V.sh = v[12]; V.z = v[13]; V.zh = v[14]; V.v = v[15];
             }
             CSRArgs A{sys.A.n, sys.A.nnz, sys.A.rowptr, sys.A.col, sys.A.val};
-            step_ctx_make(h_ctx + (size_t)s * cb, A, V, sys.b, sys.x0, sys.jacobi_diag, d_state + s, d_scr + s);
+            step_ctx_make(h_ctx + (size_t)s * cb, A, V, sys.b, sys.x0, sys.jacobi_diag, d_state + s, d_scr + s, nullptr);
             SolverState &h = h_state[s];
             memset(&h, 0, sizeof h);
             h.tol = sys.tol;

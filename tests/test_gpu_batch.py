@@ -1,9 +1,14 @@
-"""GPU parity of the batched solver (many independent systems, one persistent
-cluster launch): every system's whole history, iteration count and x are
-bitwise the CPU oracle's for that system alone, for a mix of 2D/3D
-convection-diffusion systems, classic and pipelined, with and without x0 and
-a given diagonal; invalid systems are reported and skipped without affecting
-the rest."""
+"""GPU parity of the batched solver (many independent systems: one persistent
+cluster launch, or the stepped schedule that advances all systems together
+one iteration per step): every system's whole history, iteration count and x
+are bitwise the CPU oracle's for that system alone, for a mix of 2D/3D
+convection-diffusion systems, classic and pipelined, with and without x0 and a
+given diagonal, with per-system iteration caps; invalid systems are reported
+and skipped without affecting the rest."""
+
+# the default persistent schedule, the stepped one, and the stepped one on
+# small blocks (every system on several blocks)
+SCHEDULES = (None, {"cluster": 0, "split": 0}, {"cluster": 0, "split": 256})
 import numpy as np
 import pytest
 
@@ -42,7 +47,8 @@ def _check(g, o):
     assert same_array(g["x"].cpu().numpy(), o["x"])
 
 
-def test_batch_matches_oracle_per_system(dev, orc):
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_batch_matches_oracle_per_system(dev, orc, schedule):
     import paper_2302_04180_gb300 as rbs
     work = gen.batch_workload(14, seed=3, n_min=200, n_max=9000)
     systems, refs = [], []
@@ -50,10 +56,12 @@ def test_batch_matches_oracle_per_system(dev, orc):
         b = orc.spmv(A, np.ones(A.n))
         x0 = gen.random_vector(A.n, 50 + k) if k % 4 == 1 else None
         diag = gen.random_vector(A.n, 70 + k, lo=6.0, hi=9.0) if k % 5 == 2 else None
-        systems.append(_device_system(rbs, dev, A, variant, 1e-8, 600, b=b, x0=x0, diag=diag))
-        refs.append(orc.solve(A, b, x0=x0, diag=diag, tol=1e-8, maxit=600, variant=variant))
-    res = rbs.rbs_solve_batched(systems)
+        maxit = 5 + k if k % 6 == 3 else 600  # some systems stop at their cap, unconverged
+        systems.append(_device_system(rbs, dev, A, variant, 1e-8, maxit, b=b, x0=x0, diag=diag))
+        refs.append(orc.solve(A, b, x0=x0, diag=diag, tol=1e-8, maxit=maxit, variant=variant))
+    res = rbs.rbs_solve_batched(systems, schedule=schedule)
     assert sorted({v for _, v in work}) == [0, 1]
+    assert any(o["converged"] == 0 for o in refs) and any(o["converged"] == 1 for o in refs)
     for g, o in zip(res, refs):
         _check(g, o)
 
@@ -73,7 +81,8 @@ def test_batch_equals_single_solves_and_is_repeatable(dev):
             assert same_array(x.cpu().numpy(), single["x"].cpu().numpy())
 
 
-def test_batch_reports_invalid_systems(dev, orc):
+@pytest.mark.parametrize("schedule", SCHEDULES[:2])
+def test_batch_reports_invalid_systems(dev, orc, schedule):
     import torch
     import paper_2302_04180_gb300 as rbs
     good = gen.convdiff2d(30, 20.0, (0.6, 0.8))
@@ -85,7 +94,7 @@ def test_batch_reports_invalid_systems(dev, orc):
     systems.append(dict(systems[0], maxit=0,
                         x=torch.empty(good.n, dtype=torch.float64, device=dev)))
     systems.append(_device_system(rbs, dev, good, 0, 1e-8, 500, b=np.zeros(good.n)))
-    res = rbs.rbs_solve_batched(systems)
+    res = rbs.rbs_solve_batched(systems, schedule=schedule)
     assert res[1]["status"] == rbs.RBS_EINVAL
     b = orc.spmv(good, np.ones(good.n))
     _check(res[0], orc.solve(good, b, tol=1e-8, maxit=500, variant=0))
@@ -113,7 +122,8 @@ def test_batch_results_do_not_depend_on_the_schedule(dev):
     systems = [_device_system(rbs, dev, A, v, 1e-8, 1500) for A, v in work]
     refs = _ref_solves(rbs, systems, work, 1500)
     med = int(sorted(A.n for A, _ in work)[len(work) // 2])
-    for cluster, split in ((1, 0), (2, 0), (4, med), (8, 0), (8, med), (8, 1 << 40), (16, med)):
+    for cluster, split in ((1, 0), (2, 0), (4, med), (8, 0), (8, med), (8, 1 << 40), (16, med), (0, 0), (0, 1024),
+                           (0, 64)):
         try:
             res = rbs.rbs_solve_batched(systems, schedule={"cluster": cluster, "split": split})
         except rbs.RbsError as e:
@@ -143,7 +153,7 @@ def test_batch_tuner_picks_a_schedule_and_leaves_results_unchanged(dev):
         sd["x"].fill_(-7.0)
     best = rbs.rbs_batch_tune(systems, prev=first, proxy_iters=16)
     print("tuned schedule", best)
-    assert best["cluster"] in (1, 2, 4, 8, 16) and best["split"] >= 0 and best["ms"] > 0.0
+    assert best["cluster"] in (0, 1, 2, 4, 8, 16) and best["split"] >= 0 and best["ms"] > 0.0
     for sd in systems:  # proxy solves write scratch, not the callers' x
         assert bool((sd["x"] == -7.0).all())
     res = rbs.rbs_solve_batched(systems)  # now under the tuned schedule
