@@ -91,6 +91,8 @@ def _load():
             lib.orc_jacobi_invd.argtypes = [C.c_int64, lp, ip, dp, dp, dp]
             lib.orc_jacobi_apply.restype = None
             lib.orc_jacobi_apply.argtypes = [C.c_int64, dp, dp, dp]
+            lib.orc_fma_vec.restype = None
+            lib.orc_fma_vec.argtypes = [C.c_int64, C.c_double, dp, dp, dp]
             lib.orc_set_threads.restype = None
             lib.orc_set_threads.argtypes = [C.c_int]
             lib.orc_get_threads.restype = C.c_int
@@ -128,6 +130,15 @@ def twoprod(a: float, b: float):
 
 def mul_add_unfused(a: float, b: float, c: float) -> float:
     return _load().orc_mul_add_unfused(a, b, c)
+
+
+def fma_vec(a: float, x, y):
+    """fma(a, x_i, y_i) element-wise, one rounding each."""
+    x, xp = _d(x)
+    y, yp = _d(y)
+    out = np.empty_like(x)
+    _load().orc_fma_vec(x.size, float(a), xp, yp, out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
 
 
 def set_threads(n: int) -> None:

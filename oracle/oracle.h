@@ -82,6 +82,11 @@ double orc_round_limbs(const int64_t *limbs, int32_t flags);
 void orc_set_threads(int n);
 int orc_get_threads(void);
 
+/* out_i = fma(a, x_i, y_i), one rounding each (the axpy-like steps of Fig. 2
+ * and Fig. 4, for drivers that run the loop outside this library, such as the
+ * row-block ranks of the sharded-solve test). */
+void orc_fma_vec(int64_t n, double a, const double *x, const double *y, double *out);
+
 void orc_spmv(int64_t n, const int64_t *rowptr, const int32_t *col,
               const double *val, const double *x, double *y);
 

@@ -62,6 +62,10 @@ void orc_spmv(int64_t n, const int64_t *rowptr, const int32_t *col,
     }
 }
 
+void orc_fma_vec(int64_t n, double a, const double *x, const double *y, double *out) {
+    for (int64_t i = 0; i < n; i++) out[i] = fma(a, x[i], y[i]);
+}
+
 int orc_jacobi_invd(int64_t n, const int64_t *rowptr, const int32_t *col,
                     const double *val, const double *diag, double *invd) {
     for (int64_t i = 0; i < n; i++) {

@@ -554,14 +554,20 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
 // Grid-level finish of K exact reductions held in register windows: flush the
 // windows into the block accumulators, then block_grid_finish (nblk: blocks
 // that share the reduction, 0 for the whole grid).
+// coop = false: flush every lane's window with its own atomics, without the
+// warp's shared scratch (whose bytes a timed-out asynchronous copy may still
+// overwrite).
 template <int K, int Q, int SCRATCH = FLUSH_SCRATCH>
 __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
                                              unsigned long long (*sacc)[NL], uint32_t *sflags,
                                              DotScratch *g, double *vals, bool export_limbs = false,
                                              long long *limbs_out = nullptr, int32_t *flags_out = nullptr,
-                                             unsigned nblk = 0u) {
+                                             unsigned nblk = 0u, bool coop = true) {
 #pragma unroll
-    for (int k = 0; k < K; k++) warp_flush<Q, SCRATCH>(win[k], sacc[k]);
+    for (int k = 0; k < K; k++) {
+        if (coop) warp_flush<Q, SCRATCH>(win[k], sacc[k]);
+        else win_flush<Q>(win[k], sacc[k]);
+    }
     return block_grid_finish<K>(flags, sacc, sflags, g, vals, export_limbs, limbs_out, flags_out, nblk);
 }
 

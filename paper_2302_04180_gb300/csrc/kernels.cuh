@@ -41,7 +41,10 @@ __device__ __forceinline__ double spmv_row(const CSRView &A, int64_t i, const do
 
 // Error bits that kernels OR into the workspace error word.
 constexpr unsigned ERR_INDEX = 1u;    // an out-of-range CSR index or row pointer
-constexpr unsigned ERR_TIMEOUT = 4u;  // a bounded wait on an asynchronous copy expired
+// a bounded wait on an asynchronous copy expired; the kernel's exact windows
+// must then be flushed with finish(..., coop = false), which does not use the
+// staging buffers as scratch
+constexpr unsigned ERR_TIMEOUT = 4u;
 
 // Warp-staged SpMV: each warp walks chunks of 32 consecutive rows. A chunk's
 // contiguous nonzero span (col, val), and the chunk's slice of an optional
@@ -260,9 +263,10 @@ __device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int
     SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb, b0, e0, bufs, bars);
     rowptrs(rb + step, b1, e1);
     int cur = 0;
+    SpmvChunk c1{0, CHUNK_UNSTAGED};
     for (; rb < r_end; rb += step) {
-        const SpmvChunk c1 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb + step,
-                                                       b1, e1, bufs + (cur ^ 1) * L::BUF, bars + (cur ^ 1));
+        c1 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb + step, b1, e1,
+                                        bufs + (cur ^ 1) * L::BUF, bars + (cur ^ 1));
         rowptrs(rb + 2 * step, b2, e2);
         if (c0.how == CHUNK_BULK) {
             long long spins = 0;
@@ -334,6 +338,8 @@ __device__ __forceinline__ void spmv_rows(const CSRView &A, int64_t r_begin, int
 stalled:
     // A wait ran out (ERR_TIMEOUT): stage nothing more (a late copy could still
     // land in the buffers) and read this and every later row from global memory.
+    // The call fails and its results are undefined; the kernel's exact windows
+    // are then flushed without the staging buffers as scratch (see ERR_TIMEOUT).
     err |= ERR_TIMEOUT;
     for (; rb < r_end; rb += step) {
         const int64_t r = rb + lane;
@@ -345,6 +351,19 @@ stalled:
         }
     }
     __pipeline_wait_prior(0);
+    // Bulk copies issued into the two buffers before the stall may still be in
+    // flight: wait for them (again bounded) so that none lands in this CTA's
+    // shared memory after the kernel ends. (The test stall issues none.)
+    if (!skip_bulk && lane == 0) {
+        const bool pend[2] = {c0.how == CHUNK_BULK, c1.how == CHUNK_BULK};
+        const int bufid[2] = {cur, cur ^ 1};
+        for (int k = 0; k < 2; k++) {
+            if (!pend[k]) continue;
+            long long spins = 0;
+            while (!mbar_try_wait(bars + bufid[k], (parity >> bufid[k]) & 1u) && ++spins <= wait_limit) {
+            }
+        }
+    }
     __syncwarp();
 }
 

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k1(Ct
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
+    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals, 0u, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0)
+        tail_cls_alpha(c.st, vals);
 }
 
 // K2: q = fma(-alpha, s, r), qhat = q * invd. Four blocks per SM, like K4, whose
@@ -95,7 +96,8 @@ __global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k3(Ct
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
+    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals, 0u, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0)
+        tail_cls_omega(c.st, vals);
 }
 
 // K4: x = fma(omega, qhat, fma(alpha, phat, x)), r = fma(-omega, y, q), <r0,r>, <r,r>
@@ -171,7 +173,8 @@ __global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_pipe_setu
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
+    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals, 0u, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0)
+        tail_pipe_setup(c.st, vals);
 }
 
 // Launch shape of P1 and P3 per reducer (blocks per SM; two elements per thread

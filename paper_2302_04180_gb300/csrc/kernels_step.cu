@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256, 3) k_step_cls_k1(const Ctx *ctxs, const S
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SCR>(c.g, vals, t.nblk) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
+    if (red.template finish<SCR>(c.g, vals, t.nblk, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0) tail_cls_alpha(c.st, vals);
 }
 
 __global__ void __launch_bounds__(256) k_step_cls_k2(const Ctx *ctxs, const StepTask *tasks) {
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, 3) k_step_cls_k3(const Ctx *ctxs, const S
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SCR>(c.g, vals, t.nblk) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
+    if (red.template finish<SCR>(c.g, vals, t.nblk, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0) tail_cls_omega(c.st, vals);
 }
 
 template <class R>
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256, 3) k_step_pipe_setup2(const Ctx *ctxs, co
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SCR>(c.g, vals, t.nblk) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
+    if (red.template finish<SCR>(c.g, vals, t.nblk, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0) tail_pipe_setup(c.st, vals);
 }
 
 // y = A x without a dot: the pipelined S10 (v = A zhat) and S18 / set-up (t = A what)

@@ -40,9 +40,10 @@ struct ExactR {
     // true in the last block, with vals[0..K-1] rounded (shared memory).
     // SCRATCH: the per-warp scratch size the kernel already uses, so that the
     // flush staging shares it.
+    // coop = false after a timed-out staged copy (ERR_TIMEOUT): per-lane flushes
     template <int SCRATCH = FLUSH_SCRATCH>
-    __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u) {
-        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals, false, nullptr, nullptr, nblk);
+    __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u, bool coop = true) {
+        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals, false, nullptr, nullptr, nblk, coop);
     }
 };
 
@@ -212,7 +213,8 @@ struct PlainR {
     __device__ __forceinline__ void add(int k, double x, double y) { s[k] = fma(x, y, s[k]); }
     __device__ __forceinline__ void add_sq(int k, double x) { s[k] = fma(x, x, s[k]); }
     template <int SCRATCH = 0>
-    __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u) {
+    __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u, bool coop = true) {
+        (void)coop;  // its partials live in their own shared array
         __shared__ double s_part[K][32];
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

@@ -209,3 +209,23 @@ def test_rank_split_integer_reduction_equals_single(orc):
 def test_exdot_empty_and_zero(orc):
     assert _same(orc.exdot(np.zeros(0), np.zeros(0)), 0.0)
     assert _same(orc.exdot(np.array([-0.0, 0.0]), np.array([1.0, -1.0])), 0.0)
+
+
+def test_fma_vec_is_one_rounding(orc):
+    """orc_fma_vec: fma(a, x_i, y_i) is the exact a*x_i + y_i rounded once
+    (checked against exact rationals, including cases where the unfused
+    a*x + y rounds differently)."""
+    rng = random.Random(11)
+    xs, ys, avals = [], [], []
+    for _ in range(400):
+        a = rng.uniform(-3, 3)
+        x = rng.uniform(-1, 1) * 2.0 ** rng.randrange(-30, 30)
+        y = -float(Fraction(a) * Fraction(x)) * (1 + rng.choice((0.0, 2.0 ** -52, -2.0 ** -53)))
+        xs.append(x), ys.append(y), avals.append(a)
+    differs = 0
+    for a, x, y in zip(avals, xs, ys):
+        got = orc.fma_vec(a, np.array([x]), np.array([y]))[0]
+        want = _rn_fraction(Fraction(a) * Fraction(x) + Fraction(y))
+        assert np.float64(got).view(np.uint64) == np.float64(want).view(np.uint64)
+        differs += orc.mul_add_unfused(a, x, y) != got
+    assert differs > 50
