@@ -278,7 +278,8 @@ int rbs_solve_batched(int32_t nsys, const rbs_system *systems, rbs_info *infos, 
  * through distributed shared memory), and from the first smaller one on every
  * CTA takes systems alone. cluster 0, the stepped schedule: every system
  * advances one iteration per step, one launch per phase of Fig. 2 / Fig. 4 for
- * all of them, each system on blocks of `split` rows (0: 8192), so a large
+ * all of them, each system on blocks of `split` rows (0: sized per chunk of
+ * steps from the rows still iterating, about four waves of blocks), so a large
  * system spreads over as many SMs as its rows fill (x must be 16-byte
  * aligned). `ms` is the tuner's measured time of its proxy run (0 otherwise).
  * Results never depend on the schedule: every system's iterates are bitwise
@@ -300,7 +301,7 @@ int rbs_solve_batched_ex(int32_t nsys, const rbs_system *systems, rbs_info *info
  * systems (each stopped after a number of iterations) under candidate
  * schedules -- every cluster size at the median split, then every split
  * candidate (system-size quantiles, 0 and "no cluster") at the best size, then
- * the stepped schedule at 2048, 8192 and 32768 rows per block -- and returns
+ * the stepped schedule with adaptive, 2048 and 8192 rows per block -- and returns
  * the fastest in *best, which later rbs_solve_batched calls on this
  * device use. The proxy iteration cap of system i is proxy_iters, or, given a
  * previous solve's infos (`prev`, nsys entries, nullable), proxy_iters scaled

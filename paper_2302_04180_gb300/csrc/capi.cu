@@ -93,6 +93,18 @@ cudaError_t ensure(Buf &b, size_t bytes) {
     return e;
 }
 
+// A pinned host buffer of at least `bytes` (contents not kept on growth).
+cudaError_t ensure_host(Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return cudaSuccess;
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    cudaError_t e = cudaMallocHost(&b.p, bytes);
+    if (e == cudaSuccess) b.cap = bytes;
+    return e;
+}
+
 constexpr int NVEC = 18;
 constexpr int NFLAGS = 64;
 
@@ -114,6 +126,11 @@ struct Workspace {
     std::vector<cudaEvent_t> ev_chunk;
     // graph loop: one iteration captured as the body of a conditional WHILE node
     cudaStream_t cap = nullptr;
+    // the stepped batch: a second stream for the pipelined systems' steps, its
+    // fork/join events, and pinned copies of the task list and the states
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    Buf h_tasks, h_states;  // pinned (cudaMallocHost)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::string graph_key;
@@ -184,6 +201,11 @@ void ws_free(Workspace *w) {
     if (w->graph) cudaGraphDestroy(w->graph);
     if (w->batch_exec) cudaGraphExecDestroy(w->batch_exec);
     if (w->cap) cudaStreamDestroy(w->cap);
+    if (w->side) cudaStreamDestroy(w->side);
+    if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+    if (w->ev_join) cudaEventDestroy(w->ev_join);
+    if (w->h_tasks.p) cudaFreeHost(w->h_tasks.p);
+    if (w->h_states.p) cudaFreeHost(w->h_states.p);
     delete w;
 }
 
@@ -814,7 +836,20 @@ bool schedule_ok(const rbs_batch_schedule &s) {
 int batch_stepped(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_info *infos, rbs_history *hists,
                   const rbs_batch_schedule &sched, const int32_t *proxy_maxit, float *ms) {
     const bool proxy = proxy_maxit != nullptr;
-    const int64_t rows = sched.split > 0 ? (sched.split + 63) / 64 * 64 : 8192;
+    // rows per block: fixed (split > 0), or chosen per chunk from the rows still
+    // iterating so that a launch has about four waves of 256-thread blocks --
+    // large blocks while the whole batch iterates (each block's flush and
+    // cross-block reduction is a fixed cost), small ones once few systems are
+    // left (so that they still spread over every SM)
+    const int64_t fixed_rows = sched.split > 0 ? (sched.split + 63) / 64 * 64 : 0;
+    int64_t rows = fixed_rows ? fixed_rows : 8192;
+    auto pick_rows = [&](int64_t active_rows) {
+        if (fixed_rows) return fixed_rows;
+        const int64_t waves = 4LL * w->sms * 3;
+        int64_t r = (active_rows + waves - 1) / waves;
+        r = std::max<int64_t>(1024, std::min<int64_t>(65536, r));
+        return (r + 63) / 64 * 64;
+    };
     std::vector<char> valid((size_t)nsys, 1);
     std::vector<int32_t> maxit((size_t)nsys, 0);
     size_t work_elems = 0, hist_recs = 0;
@@ -901,8 +936,13 @@ int batch_stepped(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_inf
         }
     };
     std::vector<int> cls, pipe;
+    int64_t all_rows = 0;
     for (int i = 0; i < nsys; i++)
-        if (valid[(size_t)i]) (systems[i].variant == RBS_PIPELINED ? pipe : cls).push_back(i);
+        if (valid[(size_t)i]) {
+            (systems[i].variant == RBS_PIPELINED ? pipe : cls).push_back(i);
+            all_rows += systems[i].A.n;
+        }
+    rows = pick_rows(all_rows);
     std::vector<StepTask> tasks;
     tasks_of(cls, tasks);
     const size_t ncls = tasks.size();
@@ -926,28 +966,52 @@ int batch_stepped(Workspace *w, int32_t nsys, const rbs_system *systems, rbs_inf
     CK(cudaStreamSynchronize(w->stream));
     std::vector<int32_t> ran((size_t)nsys, 0);
     auto live = [&](int i) { return !hst[(size_t)i].done && ran[(size_t)i] < maxit[(size_t)i]; };
+    // classic and pipelined systems step on two streams (independent work that
+    // fills the GPU better once few systems are left), joined after each chunk
+    if (!w->side) CK(cudaStreamCreateWithFlags(&w->side, cudaStreamNonBlocking));
+    if (!w->ev_fork) CK(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
+    if (!w->ev_join) CK(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming));
+    CK(ensure_host(w->h_states, (size_t)nsys * sizeof(SolverState)));
+    SolverState *pst = (SolverState *)w->h_states.p;
     for (;;) {
         std::vector<int> c2, p2;
         int32_t chunk = 8;
+        int64_t live_rows = 0;
         for (int i : cls)
-            if (live(i)) c2.push_back(i), chunk = std::min(chunk, maxit[(size_t)i] - ran[(size_t)i]);
+            if (live(i)) c2.push_back(i), chunk = std::min(chunk, maxit[(size_t)i] - ran[(size_t)i]),
+                         live_rows += systems[i].A.n;
         for (int i : pipe)
-            if (live(i)) p2.push_back(i), chunk = std::min(chunk, maxit[(size_t)i] - ran[(size_t)i]);
+            if (live(i)) p2.push_back(i), chunk = std::min(chunk, maxit[(size_t)i] - ran[(size_t)i]),
+                         live_rows += systems[i].A.n;
         if (c2.empty() && p2.empty()) break;
+        rows = pick_rows(live_rows);
         tasks.clear();
         tasks_of(c2, tasks);
         const size_t nc = tasks.size();
         tasks_of(p2, tasks);
-        CK(cudaMemcpyAsync(dtask, tasks.data(), tasks.size() * sizeof(StepTask), cudaMemcpyHostToDevice, w->stream));
+        // the pinned task list is rewritten only after the previous chunk's
+        // copy from it has completed (the stream was synchronised)
+        CK(ensure_host(w->h_tasks, tasks.size() * sizeof(StepTask)));
+        memcpy(w->h_tasks.p, tasks.data(), tasks.size() * sizeof(StepTask));
+        CK(cudaMemcpyAsync(dtask, w->h_tasks.p, tasks.size() * sizeof(StepTask), cudaMemcpyHostToDevice, w->stream));
+        const int np = (int)(tasks.size() - nc);
+        if (np > 0) {
+            CK(cudaEventRecord(w->ev_fork, w->stream));
+            CK(cudaStreamWaitEvent(w->side, w->ev_fork, 0));
+        }
         for (int k = 0; k < chunk; k++) {
             CK(step_iteration(w->step_ctx.p, dtask, (int)nc, RBS_CLASSIC, w->stream));
-            CK(step_iteration(w->step_ctx.p, dtask + nc, (int)(tasks.size() - nc), RBS_PIPELINED, w->stream));
+            CK(step_iteration(w->step_ctx.p, dtask + nc, np, RBS_PIPELINED, w->side));
+        }
+        if (np > 0) {
+            CK(cudaEventRecord(w->ev_join, w->side));
+            CK(cudaStreamWaitEvent(w->stream, w->ev_join, 0));
         }
         for (int i : c2) ran[(size_t)i] += chunk;
         for (int i : p2) ran[(size_t)i] += chunk;
-        // pageable host target: the copy returns once the data is there
-        CK(cudaMemcpyAsync(hst.data(), dst, (size_t)nsys * sizeof(SolverState), cudaMemcpyDeviceToHost, w->stream));
+        CK(cudaMemcpyAsync(pst, dst, (size_t)nsys * sizeof(SolverState), cudaMemcpyDeviceToHost, w->stream));
         CK(cudaStreamSynchronize(w->stream));
+        memcpy(hst.data(), pst, (size_t)nsys * sizeof(SolverState));
     }
     if (ms) {
         CK(cudaEventRecord(e1, w->stream));
@@ -1249,8 +1313,8 @@ extern "C" int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs
     if (bestc > 1)
         for (size_t k = 0; k < splits.size(); k++)
             if (k != 1 && (rc = trial(bestc, splits[k]))) return rc;
-    // the stepped schedule (cluster 0) at three block sizes
-    for (int64_t rows : {2048, 8192, 32768})
+    // the stepped schedule (cluster 0): adaptive block size, then two fixed ones
+    for (int64_t rows : {0, 2048, 8192})
         if ((rc = trial(0, rows))) return rc;
     top.ms = top_ms;
     *best = top;
