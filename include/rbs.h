@@ -324,7 +324,8 @@ int rbs_batch_tune(int32_t nsys, const rbs_system *systems, const rbs_info *prev
  * admitted when none is in flight), runs their structure check, Jacobi and
  * solver set-up, then one iteration (Fig. 2 or Fig. 4) of every system in
  * flight: one launch per phase for all of them, each system on blocks of
- * `rows_per_block` rows (0: 8192). Stopped systems (converged, breakdown, NaN,
+ * `rows_per_block` rows (0: sized per step from the rows in flight, about four
+ * waves of blocks), classic and pipelined systems on two streams. Stopped systems (converged, breakdown, NaN,
  * invalid, or maxit iterations) are retired a step or two later. A request that
  * arrives while others iterate joins them at the next step. Every answer is
  * bitwise the one rbs_solve gives for that system alone (the same element

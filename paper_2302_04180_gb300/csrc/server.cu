@@ -87,7 +87,7 @@ constexpr int DEPTH = 2;  // steps enqueued ahead of the last one read back
 struct Server {
     int device = 0;
     int slots = 64;
-    int64_t seg_rows = 8192;
+    int64_t seg_rows = 0;  // rows per block; 0: sized per step from the rows in flight
     int64_t budget = 0, in_use = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -115,8 +115,12 @@ struct Server {
 // One engine: its stream, slots and the step pipeline.
 void Server::engine_loop() {
     cudaSetDevice(device);
-    cudaStream_t st = nullptr;
+    // classic systems step on `st`, pipelined ones on `side` (forked after the
+    // step's task list is copied, joined before its scalars are read back)
+    cudaStream_t st = nullptr, side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) return;
     const int S = slots;
     const size_t cb = step_ctx_bytes();
     char *d_ctx = nullptr, *h_ctx = nullptr;
@@ -132,6 +136,10 @@ void Server::engine_loop() {
               cudaMallocHost(&h_state, S * sizeof(SolverState)) == cudaSuccess &&
               cudaMallocHost(&h_status, (size_t)RING * S * sizeof(SolverState)) == cudaSuccess;
     for (int k = 0; ok && k < RING; k++) ok = cudaEventCreateWithFlags(&ev_step[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) == cudaSuccess;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     ok = ok && cudaDeviceSynchronize() == cudaSuccess;
 
     struct Slot {
@@ -148,11 +156,14 @@ void Server::engine_loop() {
     std::vector<StepTask> tasks;
     std::vector<int> fresh;
 
+    // rows per block of this step: the server's fixed size, or (0) one sized from
+    // the rows in flight for about four waves of blocks (1024..65536 rows)
+    int64_t rows = seg_rows > 0 ? seg_rows : 8192;
     auto add_tasks = [&](int s, std::vector<StepTask> &out) {
         const int64_t n = slot[(size_t)s].n;
-        const int nblk = (int)((n + seg_rows - 1) / seg_rows);
+        const int nblk = (int)((n + rows - 1) / rows);
         for (int b = 0; b < nblk; b++)
-            out.push_back(StepTask{s, nblk, (int64_t)b * seg_rows, std::min(n, (int64_t)(b + 1) * seg_rows)});
+            out.push_back(StepTask{s, nblk, (int64_t)b * rows, std::min(n, (int64_t)(b + 1) * rows)});
     };
     auto fail_all = [&](const char *msg) {
         std::lock_guard<std::mutex> lk(mu);
@@ -287,6 +298,14 @@ void Server::engine_loop() {
             if (pool_used > pool_peak.load()) pool_peak = pool_used;
         }
         // ---- this step's task lists: admissions, then one iteration of each variant
+        if (seg_rows <= 0) {
+            int64_t flight = 0;
+            for (auto &sl : slot)
+                if (sl.ticket >= 0) flight += sl.n;
+            const int64_t waves = 4LL * sms * 3;
+            rows = std::max<int64_t>(1024, std::min<int64_t>(65536, (flight + waves - 1) / waves));
+            rows = (rows + 63) / 64 * 64;
+        }
         tasks.clear();
         int off[3];  // admissions: classic tasks [off[0], off[1]), pipelined [off[1], off[2])
         for (int var = 0; var < 2; var++) {
@@ -327,11 +346,22 @@ void Server::engine_loop() {
             ok = cudaMemcpyAsync(d_tasks[ring], h_tasks[ring], tasks.size() * sizeof(StepTask),
                                  cudaMemcpyHostToDevice, st) == cudaSuccess;
             const StepTask *T = d_tasks[ring];
-            for (int var = 0; var < 2 && ok; var++)
+            const bool pipe = off[2] > off[1] || it_cnt[1] > 0;
+            if (pipe) {
+                ok = ok && cudaEventRecord(ev_fork, st) == cudaSuccess &&
+                     cudaStreamWaitEvent(side, ev_fork, 0) == cudaSuccess;
+            }
+            for (int var = 0; var < 2 && ok; var++) {
+                cudaStream_t sv = var == RBS_CLASSIC ? st : side;
                 if (off[var + 1] > off[var])
-                    ok = step_admit(d_ctx, T + off[var], off[var + 1] - off[var], var, st) == cudaSuccess;
-            for (int var = 0; var < 2 && ok; var++)
-                if (it_cnt[var] > 0) ok = step_iteration(d_ctx, T + it_off[var], it_cnt[var], var, st) == cudaSuccess;
+                    ok = step_admit(d_ctx, T + off[var], off[var + 1] - off[var], var, sv) == cudaSuccess;
+                if (ok && it_cnt[var] > 0)
+                    ok = step_iteration(d_ctx, T + it_off[var], it_cnt[var], var, sv) == cudaSuccess;
+            }
+            if (pipe) {
+                ok = ok && cudaEventRecord(ev_join, side) == cudaSuccess &&
+                     cudaStreamWaitEvent(st, ev_join, 0) == cudaSuccess;
+            }
         }
         ok = ok && cudaMemcpyAsync(h_status + (size_t)ring * S, d_state, S * sizeof(SolverState),
                                    cudaMemcpyDeviceToHost, st) == cudaSuccess;
@@ -355,6 +385,7 @@ void Server::engine_loop() {
         }
     }
     if (!ok) fail_all("the serving engine met a CUDA error");
+    cudaStreamSynchronize(side);
     cudaStreamSynchronize(st);
     for (auto &sl : slot)
         if (sl.mem && sl.ticket >= 0) cudaFreeAsync(sl.mem, st);
@@ -370,6 +401,10 @@ void Server::engine_loop() {
     cudaFreeHost(h_ctx);
     cudaFreeHost(h_state);
     cudaFreeHost(h_status);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    cudaStreamSynchronize(side);
+    cudaStreamDestroy(side);
     cudaStreamDestroy(st);
 }
 
@@ -391,7 +426,7 @@ int rbs_server_create(int32_t engines, int32_t max_active, int64_t budget_bytes,
     }
     s->slots = max_active;
     s->budget = budget_bytes;
-    s->seg_rows = rows_per_block > 0 ? (rows_per_block + 63) / 64 * 64 : 8192;
+    s->seg_rows = rows_per_block > 0 ? (rows_per_block + 63) / 64 * 64 : 0;
     cudaMemPoolProps props;
     memset(&props, 0, sizeof props);
     props.allocType = cudaMemAllocationTypePinned;
