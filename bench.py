@@ -634,7 +634,8 @@ def _kernel_micro(rbs, gen, dev, futs):
     out["spmv_poisson128"] = {"us": ms * 1e3, "GB/s": byt / (ms * 1e-3) / 1e9, "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / hbm}
     del Ad, xv, yv
     # the 27-point e-type stencil at the paper's scalability size (159^3 =
-    # 4,019,679 unknowns, 27 nonzeros per interior row: long-span staging)
+    # 4,019,679 unknowns, 27 nonzeros per interior row: the register-staged
+    # long-row schedule)
     A = gen.stencil27(159)
     Ad = rbs.to_device(A, dev)
     xv = torch.from_numpy(gen.random_vector(A.n, 1)).to(dev)

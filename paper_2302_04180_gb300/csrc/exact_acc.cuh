@@ -373,14 +373,14 @@ __device__ __forceinline__ void exact_add2(Win<Q> &H, Win<Q> &Lw, uint32_t &flag
 constexpr int MAX_WARPS = 8;                        // every kernel here runs blocks of at most 256 threads
 constexpr int FLUSH_SCRATCH = 32 * 8 * 8 + 32 * 4;  // bytes of the warp_flush staging
 
-// Each warp's private slice of one shared buffer of BYTES per warp. Phases of
-// a kernel that stage data per warp (SpMV operands, then the window flush)
-// reuse it by naming the same BYTES; a warp only ever touches its own slice,
-// so no block barrier is needed between them.
-template <int BYTES>
+// Each warp's private slice of one shared buffer of BYTES per warp, for blocks
+// of at most WARPS warps. Phases of a kernel that stage data per warp (SpMV
+// operands, then the window flush) reuse it by naming the same BYTES; a warp
+// only ever touches its own slice, so no block barrier is needed between them.
+template <int BYTES, int WARPS = MAX_WARPS>
 __device__ __forceinline__ unsigned char *warp_scratch() {
     static_assert(BYTES % 16 == 0, "16-byte aligned slices");
-    __shared__ __align__(16) unsigned char buf[MAX_WARPS * BYTES];
+    __shared__ __align__(16) unsigned char buf[WARPS * BYTES];
     return buf + (threadIdx.x >> 5) * BYTES;
 }
 

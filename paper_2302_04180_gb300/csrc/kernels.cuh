@@ -367,6 +367,171 @@ stalled:
     __syncwarp();
 }
 
+// Long rows through registers (rows of up to SPMV_REG_LEN nonzeros, e.g. the
+// 27-point stencil). The row product is a chain of dependent fmas, and on this
+// GPU one warp's chain already keeps an SM sub-partition's FP64 unit busy: the
+// kernel is bound by that unit once a chain is ready on every sub-partition at
+// all times. spmv_rows holds two staging buffers per warp for the whole of a
+// chunk's chain, which leaves room for 8 warps per SM; here each warp has ONE
+// buffer, and moves the chunk into registers as soon as it lands: every lane
+// gathers its row's x entries (all at once) and loads its row's values, after
+// which the buffer is refilled with the next chunk while the chain runs from
+// registers. Three 4-warp blocks fit per SM. Chunks with a longer row, or not
+// staged, are computed as in spmv_rows before the refill. Staging, the bounded
+// waits, the index checks and the timeout fallback are those of spmv_rows; the
+// arithmetic is exactly spmv_row's.
+constexpr int SPMV_REG_LEN = 28;
+constexpr int SPMV_REG_WARPS = 4;  // warps per block of the kernels using spmv_rows_reg
+template <bool CHECKED, int CAP, bool L2X, class F>
+__device__ __forceinline__ void spmv_rows_reg(const CSRView &A, int64_t r_begin, int64_t r_end, int64_t warp,
+                                              int64_t nwarps, const double *__restrict__ x,
+                                              const double *__restrict__ z, bool z_bulk, bool test_stall,
+                                              unsigned &err, F &&fn) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int G = SPMV_REG_LEN;
+    __shared__ __align__(8) unsigned long long s_bar[SPMV_REG_WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t step = nwarps * 32;
+    int64_t rb = r_begin + warp * 32;
+    const unsigned ncol = A.n < 0x80000000LL ? (unsigned)A.n : 0x80000000u;
+    const bool wide = ((reinterpret_cast<uintptr_t>(A.col) | reinterpret_cast<uintptr_t>(A.val)) & 15) == 0;
+    const bool bulk_ok = wide && (!z_bulk || (reinterpret_cast<uintptr_t>(z) & 15) == 0);
+    using L = SpmvLayout<CAP>;
+    unsigned char *buf = warp_scratch<L::BUF, SPMV_REG_WARPS>();
+    unsigned long long *bar = s_bar + wid;
+    if (lane == 0) {
+        mbar_init(bar);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncwarp();
+    unsigned parity = 0u;
+    const long long wait_limit = test_stall ? SPMV_TEST_WAIT_LIMIT : SPMV_WAIT_LIMIT;
+    const bool skip_bulk = test_stall;
+    auto rowptrs = [&](int64_t r0, long long &b, long long &e) {
+        const int64_t r = r0 + lane;
+        b = 0;
+        e = 0;
+        if (r0 < r_end && r < r_end) {
+            b = A.rowptr[r];
+            e = A.rowptr[r + 1];
+        }
+    };
+    long long b0, e0, b1, e1, b2, e2;
+    rowptrs(rb, b0, e0);
+    SpmvChunk c0 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb, b0, e0, buf, bar);
+    rowptrs(rb + step, b1, e1);
+    for (; rb < r_end; rb += step) {
+        if (c0.how == CHUNK_BULK) {
+            long long spins = 0;
+            while (!mbar_try_wait(bar, parity))
+                if (++spins > wait_limit) break;
+            if (__any_sync(FULL, spins > wait_limit)) goto stalled;
+            parity ^= 1u;
+        }
+        __pipeline_wait_prior(0);  // chunk rb's per-lane copies have landed
+        __syncwarp();
+        {
+            const int64_t r = rb + lane;
+            const bool live = r < r_end;
+            const int len = live ? (int)(e0 - b0) : 0;
+            const bool reg = c0.how != CHUNK_UNSTAGED && __all_sync(FULL, len <= G);
+            const int lmax = (int)__reduce_max_sync(FULL, (unsigned)(len > 0 ? len : 0));
+            double acc = 0.0, zr = 0.0;
+            double xv[G], vv[G];
+            if (reg) {
+                if (live && len > 0) {
+                    const int32_t *scol =
+                        reinterpret_cast<const int32_t *>(buf + L::COL_OFF) + (b0 - spmv_ca(c0.B, wide));
+                    const double *sval =
+                        reinterpret_cast<const double *>(buf + L::VAL_OFF) + (b0 - spmv_va(c0.B, wide));
+                    unsigned cmax = 0u;
+                    // every gather of the row in flight at once (entries past the
+                    // row's end repeat its last one and are not used)
+#pragma unroll
+                    for (int j = 0; j < G; j++) {
+                        const int k = j < len ? j : len - 1;
+                        const unsigned cidx = (unsigned)scol[k];
+                        if (CHECKED) {
+                            cmax = max(cmax, cidx);
+                            xv[j] = L2X ? __ldcg(x + min(cidx, ncol - 1u)) : __ldg(x + min(cidx, ncol - 1u));
+                        } else {
+                            xv[j] = L2X ? __ldcg(x + cidx) : __ldg(x + cidx);
+                        }
+                        vv[j] = sval[k];
+                    }
+                    if (CHECKED && cmax >= ncol) err |= ERR_INDEX;
+                }
+                if (z && live) zr = reinterpret_cast<const double *>(buf)[lane];
+            } else if (live) {
+                if (c0.how != CHUNK_UNSTAGED) {
+                    const int32_t *scol =
+                        reinterpret_cast<const int32_t *>(buf + L::COL_OFF) + (b0 - spmv_ca(c0.B, wide));
+                    const double *sval =
+                        reinterpret_cast<const double *>(buf + L::VAL_OFF) + (b0 - spmv_va(c0.B, wide));
+                    unsigned cmax = 0u;
+                    for (int k = 0; k < len; k++) {
+                        const unsigned cidx = (unsigned)scol[k];
+                        if (CHECKED) cmax = max(cmax, cidx);
+                        const unsigned c = CHECKED ? min(cidx, ncol - 1u) : cidx;
+                        acc = fma(sval[k], L2X ? __ldcg(x + c) : __ldg(x + c), acc);
+                    }
+                    if (CHECKED && len > 0 && cmax >= ncol) err |= ERR_INDEX;
+                    if (z) zr = reinterpret_cast<const double *>(buf)[lane];
+                } else {
+                    bool bad = false;
+                    acc = spmv_row<L2X>(A, r, x, bad);
+                    if (bad) err |= ERR_INDEX;
+                    if (z) zr = z[r];
+                }
+            }
+            __syncwarp();  // every lane is done with the buffer: refill it
+            c0 = spmv_prepare<CHECKED, CAP>(A, r_end, z, wide, bulk_ok, z_bulk, skip_bulk, rb + step, b1, e1, buf,
+                                            bar);
+            rowptrs(rb + 2 * step, b2, e2);
+            if (reg && live) {
+                // the chain in stored order, cut at the warp's longest row in
+                // groups of 4 (a warp-uniform branch)
+#pragma unroll
+                for (int g = 0; g < G; g += 4) {
+                    if (g >= lmax) break;
+#pragma unroll
+                    for (int j = g; j < g + 4; j++)
+                        if (j < len) acc = fma(vv[j], xv[j], acc);
+                }
+            }
+            if (live) fn(r, acc, zr);
+        }
+        b0 = b1;
+        e0 = e1;
+        b1 = b2;
+        e1 = e2;
+    }
+    __pipeline_wait_prior(0);
+    __syncwarp();
+    return;
+stalled:
+    // A wait ran out (ERR_TIMEOUT): as in spmv_rows, stage nothing more and
+    // read this and every later row from global memory, then wait (bounded)
+    // for the copy still in flight into the buffer.
+    err |= ERR_TIMEOUT;
+    for (; rb < r_end; rb += step) {
+        const int64_t r = rb + lane;
+        if (r < r_end) {
+            bool bad = false;
+            const double acc = spmv_row<L2X>(A, r, x, bad);
+            if (bad) err |= ERR_INDEX;
+            fn(r, acc, z ? z[r] : 0.0);
+        }
+    }
+    __pipeline_wait_prior(0);
+    if (!skip_bulk && lane == 0) {
+        long long spins = 0;
+        while (!mbar_try_wait(bar, parity) && ++spins <= wait_limit) {
+        }
+    }
+    __syncwarp();
+}
+
 // The whole matrix over the grid: every warp of every block.
 template <bool CHECKED, int CAP, class F>
 __device__ __forceinline__ void spmv_warp_rows(const CSRView &A, const double *__restrict__ x,

@@ -173,12 +173,26 @@ cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, doubl
 // standalone product); without it the solver has validated the structure at
 // set-up. With a solver state, the kernel is a no-op once the solver stopped.
 template <bool CHECKED, int CAP>
-__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3)
+__global__ void __launch_bounds__(256, 3)
     k_spmv(CSRView A, const double *__restrict__ x, double *__restrict__ y, const SolverState *st, unsigned *err,
            int mode) {
     if (st && st->done) return;
     unsigned eb = 0u;
     spmv_each<CHECKED, CAP>(A, x, nullptr, mode, eb, [&](int64_t i, double v, double) { y[i] = v; });
+    if (eb) atomicOr(err, eb);
+}
+
+// y = A x for long rows (mode 3): register-staged chunks (spmv_rows_reg) in
+// 4-warp blocks, three resident per SM.
+template <bool CHECKED>
+__global__ void __launch_bounds__(SPMV_REG_WARPS * 32, 3)
+    k_spmv_reg(CSRView A, const double *__restrict__ x, double *__restrict__ y, const SolverState *st,
+               unsigned *err, int mode) {
+    if (st && st->done) return;
+    unsigned eb = 0u;
+    spmv_rows_reg<CHECKED, SPMV_CAP_LONG, false>(
+        A, 0, A.n, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), (int64_t)gridDim.x * (blockDim.x >> 5),
+        x, nullptr, true, (mode & SPMV_TEST_STALL) != 0, eb, [&](int64_t i, double v, double) { y[i] = v; });
     if (eb) atomicOr(err, eb);
 }
 
@@ -197,20 +211,22 @@ static void spmv_carveout(int c) {
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && applied[dev] != c) {
         cudaFuncSetAttribute(k_spmv<true, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
         cudaFuncSetAttribute(k_spmv<false, SPMV_CAP_SHORT>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-        const int cl = c < 0 ? c : 100;  // the long-row kernels need (nearly) all of it
-        cudaFuncSetAttribute(k_spmv<true, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
-        cudaFuncSetAttribute(k_spmv<false, SPMV_CAP_LONG>, cudaFuncAttributePreferredSharedMemoryCarveout, cl);
+        // the long-row kernel needs all of it, whatever the knob says
+        cudaFuncSetAttribute(k_spmv_reg<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(k_spmv_reg<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaGetLastError();
         applied[dev] = c;
     }
 }
 
+// Resident blocks per SM of the SpMV kernel of `mode` at this block size (the
+// long-row kernel: at its own block of SPMV_REG_WARPS warps).
 int spmv_blocks_per_sm(int block, int carveout, int mode) {
     spmv_carveout(carveout);
     int nb = 0;
-    const cudaError_t e =
-        mode == SPMV_MODE_LONG ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true, SPMV_CAP_LONG>, block, 0)
-                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true, SPMV_CAP_SHORT>, block, 0);
+    const cudaError_t e = mode == SPMV_MODE_LONG
+                              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv_reg<true>, SPMV_REG_WARPS * 32, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_spmv<true, SPMV_CAP_SHORT>, block, 0);
     if (e != cudaSuccess || nb < 1) {
         cudaGetLastError();
         nb = 1;
@@ -218,14 +234,47 @@ int spmv_blocks_per_sm(int block, int carveout, int mode) {
     return nb;
 }
 
+// The long-row kernel runs its own launch shape: blocks of SPMV_REG_WARPS
+// warps, all of them resident (cfg's grid and block are not used).
+static Cfg spmv_reg_cfg(int64_t n, int carveout) {
+    static std::mutex mu;
+    static int sms[64], bps[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int nsm, nb;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!sms[dev]) {
+            int v = 0;
+            if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+                cudaGetLastError();
+                v = 1;
+            }
+            bps[dev] = spmv_blocks_per_sm(SPMV_REG_WARPS * 32, carveout, SPMV_MODE_LONG);
+            sms[dev] = v;
+        }
+        nsm = sms[dev];
+        nb = bps[dev];
+    }
+    Cfg c;
+    c.block = SPMV_REG_WARPS * 32;
+    const int64_t need = (n + c.block - 1) / c.block, cap = (int64_t)nsm * nb;
+    c.grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
+    return c;
+}
+
 cudaError_t launch_spmv(const CSRArgs &A, const double *x, double *y, const SolverState *st,
                         unsigned *err, Cfg cfg, cudaStream_t s) {
     spmv_carveout(cfg.carveout);
-    const bool lng = (cfg.mode & SPMV_MODE_MASK) == SPMV_MODE_LONG;
-    if (st && lng) k_spmv<false, SPMV_CAP_LONG><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
-    else if (st) k_spmv<false, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
-    else if (lng) k_spmv<true, SPMV_CAP_LONG><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
-    else k_spmv<true, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    if ((cfg.mode & SPMV_MODE_MASK) == SPMV_MODE_LONG) {
+        const Cfg r = spmv_reg_cfg(A.n, cfg.carveout);
+        if (st) k_spmv_reg<false><<<r.grid, r.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+        else k_spmv_reg<true><<<r.grid, r.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    } else if (st) {
+        k_spmv<false, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    } else {
+        k_spmv<true, SPMV_CAP_SHORT><<<cfg.grid, cfg.block, 0, s>>>(view(A), x, y, st, err, cfg.mode);
+    }
     return cudaGetLastError();
 }
 

@@ -67,18 +67,47 @@ def test_poisson_128_full_size(rbs, dev, orc):
     rbs.rbs_set_param("spmv.mode", 0)
 
 
-def test_bad_column_is_reported_not_read(rbs, dev):
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_bad_column_is_reported_not_read(rbs, dev, mode):
     import torch
-    A = gen.random_csr(100, 5, seed=1)
+    A = gen.random_csr(100, 5, seed=1) if mode != 3 else gen.stencil27(7)
     col = A.col.copy()
     col[len(col) // 2] = 1 << 30
     bad = gen.CSR(A.n, A.rowptr, col, A.val)
     Ad = rbs.to_device(bad, dev)
-    rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
-    with pytest.raises(rbs.RbsError) as e:
-        rbs.rbs_stream_status()
-    assert e.value.code == rbs.RBS_EINVAL
-    rbs.rbs_stream_status()  # cleared
+    try:
+        rbs.rbs_set_param("spmv.mode", mode)
+        rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+        with pytest.raises(rbs.RbsError) as e:
+            rbs.rbs_stream_status()
+        assert e.value.code == rbs.RBS_EINVAL
+        rbs.rbs_stream_status()  # cleared
+    finally:
+        rbs.rbs_set_param("spmv.mode", 0)
+
+
+@pytest.mark.parametrize("side", [7, 21, 33])
+def test_stencil27_ragged_chunks(rbs, dev, orc, side):
+    """Long rows (27 nonzeros) through the register-staged schedule: n = 343,
+    9261 and 35937 leave tails of 23, 13 and 1 rows after the 32-row chunks;
+    the edge rows (8 to 18 nonzeros) share chunks with the interior ones."""
+    A = gen.stencil27(side)
+    x = gen.random_vector(A.n, side) * 10.0 ** gen.random_vector(A.n, side + 1, 9, -30, 30)
+    x[::7] = -0.0
+    ref = orc.spmv(A, x)
+    for mode in (0, 3):
+        rbs.rbs_set_param("spmv.mode", mode)
+        assert same_array(_spmv(rbs, dev, A, x), ref), mode
+    rbs.rbs_set_param("spmv.mode", 0)
+
+
+def test_stencil27_159_full_size(rbs, dev, orc):
+    """The 27-point e-type matrix at the benchmark's size (n = 4,019,679,
+    nnz = 107,171,875), every row bitwise the oracle's."""
+    A = gen.stencil27(159)
+    assert A.n == 159 ** 3 and A.nnz == (3 * 159 - 2) ** 3
+    x = gen.random_vector(A.n, 27)
+    assert same_array(_spmv(rbs, dev, A, x), orc.spmv(A, x))
 
 
 def test_jacobi(rbs, dev, orc):

@@ -13,11 +13,13 @@ from paper_2302_04180_gb300 import gen
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_runs_out_and_is_reported(orc):
+@pytest.mark.parametrize("make", [lambda: gen.poisson3d(24), lambda: gen.stencil27(19)],
+                         ids=["short_rows", "long_rows"])
+def test_bounded_wait_runs_out_and_is_reported(orc, make):
     import torch
     dev = cuda_device()
     import paper_2302_04180_gb300 as rbs
-    A = gen.poisson3d(24)
+    A = make()
     Ad = rbs.to_device(A, dev)
     x = gen.random_vector(A.n, 8)
     xt = torch.from_numpy(x).to(dev)
