@@ -438,19 +438,15 @@ __device__ __forceinline__ long long partial_norm(const unsigned long long *L, i
 }
 
 // Round an exact value given as carry-save signed limbs (|limb| < 2^62) once
-// to nearest even. G is modified (normalised in place). One thread.
-static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t flags) {
+// to nearest even, given its lowest and highest nonzero limbs lo and hi (lo =
+// -1 or lo > hi: the value is zero). G is modified (normalised in place). One
+// thread.
+static __device__ __noinline__ double round_limbs_span(long long *G, uint32_t flags, int lo, int hi) {
     if (flags & F_NAN) return qnan();
     if ((flags & F_PINF) && (flags & F_NINF)) return qnan();
     if (flags & F_PINF) return __longlong_as_double(0x7ff0000000000000ll);
     if (flags & F_NINF) return __longlong_as_double((long long)0xfff0000000000000ull);
-    int lo = -1, hi = -1;
-    for (int j = 0; j < NL; j++)
-        if (G[j] != 0) {
-            if (lo < 0) lo = j;
-            hi = j;
-        }
-    if (lo < 0) return 0.0;
+    if (lo < 0 || lo > hi) return 0.0;
     // carry propagation from lo up; two limbs past hi the carry is 0 or -1
     int top = hi + 2 < NL - 1 ? hi + 2 : NL - 1;
     long long c = 0;
@@ -503,6 +499,17 @@ static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t 
     return __longlong_as_double((long long)bits);
 }
 
+// round_limbs_span after a scan of all NL limbs for the nonzero span.
+static __device__ __noinline__ double round_limbs_thread(long long *G, uint32_t flags) {
+    int lo = -1, hi = -1;
+    for (int j = 0; j < NL; j++)
+        if (G[j] != 0) {
+            if (lo < 0) lo = j;
+            hi = j;
+        }
+    return round_limbs_span(G, flags, lo, hi);
+}
+
 // Block- and grid-level finish of K exact reductions, once every thread's own
 // accumulators are in the block accumulators sacc (flags[k]: this thread's
 // non-finite flags). Every thread of each of the nblk blocks that share the
@@ -515,6 +522,13 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
                                                   uint32_t *sflags, DotScratch *g, double *vals,
                                                   bool export_limbs = false, long long *limbs_out = nullptr,
                                                   int32_t *flags_out = nullptr, unsigned nblk = 0u) {
+    // nonzero limb span of each reduction, found while the last block reads
+    // the limbs back (so that its rounding need not scan all NL of them)
+    __shared__ int s_span[K][2];
+    if (threadIdx.x < K) {
+        s_span[threadIdx.x][0] = NL;
+        s_span[threadIdx.x][1] = -1;
+    }
 #pragma unroll
     for (int k = 0; k < K; k++)
         if (flags[k]) atomicOr(&sflags[k], flags[k]);
@@ -535,7 +549,12 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
     // read back (and clear) the global accumulators into shared memory
     for (int idx = threadIdx.x; idx < K * NL; idx += blockDim.x) {
         const int k = idx / NL, j = idx - k * NL;
-        sacc[k][j] = atomicExch(&g->limbs[k][j], 0ull);
+        const unsigned long long v = atomicExch(&g->limbs[k][j], 0ull);
+        sacc[k][j] = v;
+        if (v) {
+            atomicMin(&s_span[k][0], j);
+            atomicMax(&s_span[k][1], j);
+        }
     }
     if (threadIdx.x < K) sflags[threadIdx.x] = atomicExch(&g->flags[threadIdx.x], 0u);
     if (threadIdx.x == 0) g->ticket = 0u;
@@ -546,7 +565,9 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
         if (threadIdx.x == 0) *flags_out = (int32_t)sflags[0];
         return true;
     }
-    if (threadIdx.x < K) vals[threadIdx.x] = round_limbs_thread((long long *)sacc[threadIdx.x], sflags[threadIdx.x]);
+    if (threadIdx.x < K)
+        vals[threadIdx.x] = round_limbs_span((long long *)sacc[threadIdx.x], sflags[threadIdx.x],
+                                             s_span[threadIdx.x][0], s_span[threadIdx.x][1]);
     __syncthreads();
     return true;
 }

@@ -1,6 +1,8 @@
 // Standalone kernels: exact dot (single and multi-output), long-accumulator
 // export and rounding, fma-ordered SpMV, Jacobi, CSR validation.
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -126,11 +128,30 @@ static int exdot_occ_q(int k, int block) {
     return nb;
 }
 
+// Cached per device and kernel variant: the query costs a few microseconds of
+// host time, which a short dot would otherwise pay on every call.
 int exdot_blocks_per_sm(int k, int window, int block, int64_t n) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, bool>, int> cache;
     const bool smem = k <= 2 && n >= EXDOT_SMEM_MIN_N;
-    if (window == 2) return smem ? exdot_occ_q<2, true>(k, block) : exdot_occ_q<2, false>(k, block);
-    if (window == 1) return smem ? exdot_occ_q<1, true>(k, block) : exdot_occ_q<1, false>(k, block);
-    return smem ? exdot_occ_q<4, true>(k, block) : exdot_occ_q<4, false>(k, block);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    const auto key = std::make_tuple(dev, k, window, block, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int nb;
+    if (window == 2) nb = smem ? exdot_occ_q<2, true>(k, block) : exdot_occ_q<2, false>(k, block);
+    else if (window == 1) nb = smem ? exdot_occ_q<1, true>(k, block) : exdot_occ_q<1, false>(k, block);
+    else nb = smem ? exdot_occ_q<4, true>(k, block) : exdot_occ_q<4, false>(k, block);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = nb;
+    return nb;
 }
 
 cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,

@@ -159,11 +159,14 @@ struct ExactS {
 #pragma unroll
         for (int j = 0; j < 5; j++) p[j * NT] += (long long)u[j];
     }
-    // Warp-cooperative flush of every lane's window k (all 32 lanes call it):
-    // the lanes' windows usually sit on the same limbs, so per-lane atomics
-    // would collide 32 ways; instead lane j sums every lane's digit of limb
-    // lo + j straight from shared memory and adds it with one atomic.
-    // Windows spread over more than 32 limbs fall back to per-lane flushes.
+    // Warp-cooperative flush of every lane's window k at the end of the kernel
+    // (all 32 lanes call it; the digits are left as they are). The lanes'
+    // windows usually sit on the same limbs, so per-lane atomics would collide
+    // 32 ways. When every non-empty window has the same anchor, each digit is
+    // summed over the warp with shuffles (each lane reads its own digits:
+    // conflict-free) and lane j adds digit j's sum with one atomic. Otherwise,
+    // with anchors at most 32 - W limbs apart, lane j sums every lane's digit
+    // of limb lo + j from shared memory; wider spreads flush per lane.
     __device__ __forceinline__ void flush_warp(int k) {
         const unsigned FULL = 0xffffffffu;
         const int lane = threadIdx.x & 31;
@@ -171,6 +174,20 @@ struct ExactS {
         const int lo = (int)__reduce_min_sync(FULL, (unsigned)(has ? a[k] : 0x7fffffff));
         const int hi = (int)__reduce_max_sync(FULL, (unsigned)(has ? a[k] : 0));
         if (lo == 0x7fffffff) return;
+        if (lo == hi) {
+            const long long *pp = win + (k * 2 * W) * NT + threadIdx.x, *pn = pp + W * NT;
+            long long mine = 0;
+#pragma unroll
+            for (int j = 0; j < W; j++) {
+                long long d = has ? pp[j * NT] - pn[j * NT] : 0;  // |d| < 2^52: the warp sum < 2^57
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULL, d, o);
+                if (lane == j) mine = d;
+            }
+            if (lane < W && mine && lo + lane < NL) sacc_add(&sacc[k][lo + lane], mine);
+            a[k] = WIN_EMPTY;
+            return;
+        }
         if (hi - lo > 32 - W) {
             flush(k);
             return;
@@ -182,9 +199,6 @@ struct ExactS {
             const int j = lo + lane - al;
             if (al >= 0 && j >= 0 && j < W) sum += w0[j * NT + l] - w0[(W + j) * NT + l];
         }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 2 * W; j++) win[(k * 2 * W + j) * NT + threadIdx.x] = 0;
         if (sum && lo + lane < NL) sacc_add(&sacc[k][lo + lane], sum);
         a[k] = WIN_EMPTY;
     }

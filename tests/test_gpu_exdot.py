@@ -134,6 +134,27 @@ def test_launch_shape_and_window_independence(rbs, dev, orc):
     assert seen == {int(bits(ref))}
 
 
+def test_long_dot_any_launch_shape(rbs, dev, orc):
+    """Long dots (the shared-memory windows, n >= 2^23) under any launch shape:
+    one block, a few blocks, whole waves and more blocks than fit at once, two
+    block sizes; n odd. Every result is the oracle's, bit for bit."""
+    import torch
+    n = (1 << 23) + 13
+    x, y, _ = gen.ill_conditioned_dot(n, 1e32, 11)
+    ref = int(bits(orc.exdot(x, y)))
+    xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+    try:
+        for block in (64, 256):
+            for grid in (1, 5, 608, 1500):
+                rbs.rbs_set_param("exdot.block", block)
+                rbs.rbs_set_param("exdot.grid", grid)
+                assert int(bits(rbs.rbs_exdot(xt, yt).item())) == ref, (block, grid)
+    finally:
+        rbs.rbs_set_param("exdot.grid", 0)
+        rbs.rbs_set_param("exdot.block", 0)
+    assert int(bits(rbs.rbs_exdot(xt, yt).item())) == ref
+
+
 def test_run_to_run(rbs, dev, orc):
     import torch
     x, y, _ = gen.ill_conditioned_dot(1 << 21, 1e32, 7)
