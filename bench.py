@@ -767,6 +767,40 @@ def _trace_buckets(traces, width=25):
     return out
 
 
+def run_micro_spmv(args):
+    """Standalone CSR SpMV on the named matrices (poisson:SIDE, the 7-point
+    Poisson matrix; stencil27:SIDE, the 27-point e-type one), one JSON line per
+    case; the profiling target of the SpMV kernels."""
+    import torch
+    import paper_2302_04180_gb300 as rbs
+    from paper_2302_04180_gb300 import gen
+    dev = torch.device("cuda:0")
+    hbm, _ = _peaks()
+    makers = {"poisson": gen.poisson3d, "stencil27": gen.stencil27}
+    for case in args.micro_spmv.split(","):
+        kind, side = case.split(":")
+        A = makers[kind](int(side))
+        Ad = rbs.to_device(A, dev)
+        xv = torch.from_numpy(gen.random_vector(A.n, 1)).to(dev)
+        yv = torch.empty_like(xv)
+        for _ in range(args.warmup):
+            rbs.rbs_spmv_csr(Ad, xv, yv)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            rbs.rbs_spmv_csr(Ad, xv, yv)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / max(args.steps, 1)
+        byt = 12 * A.nnz + 8 * (A.n + 1) + 16 * A.n
+        print(json.dumps({"kernel": "spmv", "matrix": case, "n": int(A.n), "nnz": int(A.nnz), "us": ms * 1e3,
+                          "GB/s": byt / (ms * 1e-3) / 1e9, "frac_of_hbm": byt / (ms * 1e-3) / 1e9 / hbm}),
+              flush=True)
+        del Ad, xv, yv
+    return 0
+
+
 def run_micro_exdot(args):
     """Standalone exact dots of seeded ill-conditioned vectors with known exact
     results (the kernel microbenchmark's dot cases), one JSON line per case."""
@@ -826,6 +860,9 @@ def main():
     ap.add_argument("--micro-exdot", default=None, metavar="LOG2N:COND[,...]",
                     help="only the standalone exact-dot microbenchmark on these cases "
                          "(e.g. 24:1e32 or 20:1,27:1e48); the profiling target of the exdot")
+    ap.add_argument("--micro-spmv", default=None, metavar="KIND:SIDE[,...]",
+                    help="only the standalone SpMV microbenchmark on these matrices "
+                         "(e.g. stencil27:159 or poisson:128); the profiling target of the SpMV")
     args = ap.parse_args()
     global GRID
     GRID = args.grid
@@ -835,6 +872,8 @@ def main():
         return run_serving(args)
     if args.micro_exdot:
         return run_micro_exdot(args)
+    if args.micro_spmv:
+        return run_micro_spmv(args)
     if args.solve_only:
         return run_solve_only(args)
     return run_gpu(args)
