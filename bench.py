@@ -321,6 +321,7 @@ def run_gpu(args):
     pipelined = {"value": rq_["iters"] / (time.perf_counter() - t0), "iters": rq_["iters"],
                  "converged": rq_["converged"]}
     c3b = _c3b(rbs, gen, dev)
+    c27 = _c27(rbs, gen, dev)
     kernels = _kernel_micro(rbs, gen, dev, futs)
     pool.shutdown()
     import shutil
@@ -336,7 +337,8 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
             "plain_comparator": plain,
-            "pipelined": pipelined, "c1_poisson16": c1, "c3b_convdiff192": c3b, "kernels": kernels,
+            "pipelined": pipelined, "c1_poisson16": c1, "c3b_convdiff192": c3b, "stencil27_159": c27,
+            "kernels": kernels,
             "batched": batched, "serving": serving}
     if args.cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(A, b.cpu().numpy())
@@ -669,6 +671,36 @@ def _c1(rbs, gen, dev, reps=30):
         dt = time.perf_counter() - t
         out[name] = {"iters_per_s": its / dt, "us_per_iter": dt / its * 1e6, "iters": r["iters"],
                      "solves_per_s": reps / dt}
+    return out
+
+
+def _c27(rbs, gen, dev, reps=3):
+    """The paper's scalability workload (Sec. 5.2), the 27-point e-type
+    stencil, at 159^3 (n = 4,019,679, nnz = 107,171,875): classic and pipelined
+    reproducible solves to tol 1e-10, iterations/s and the whole iteration's
+    algorithmic bytes against the HBM peak (classic: two SpMV + dot passes of
+    12 nnz + 32 n + 8 bytes and 152 n bytes of vector updates; pipelined: two
+    SpMV of 12 nnz + 24 n + 8 and 304 n bytes in P1 and P3)."""
+    import torch
+    A = gen.stencil27(159)
+    Ad = rbs.to_device(A, dev)
+    b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+    x = torch.empty(A.n, dtype=torch.float64, device=dev)
+    hbm, _ = _peaks()
+    per_iter = {"classic": 2 * (12 * A.nnz + 32 * A.n + 8) + 152 * A.n,
+                "pipelined": 2 * (12 * A.nnz + 24 * A.n + 8) + 304 * A.n}
+    out = {"n": int(A.n), "nnz": int(A.nnz)}
+    for name, v in (("classic", 0), ("pipelined", 1)):
+        rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=v, x_out=x, history=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        its = 0
+        for _ in range(reps):
+            its += rbs.rbs_solve(Ad, b, tol=TOL, maxit=MAXIT, variant=v, x_out=x, history=False)["iters"]
+        torch.cuda.synchronize()
+        ips = its / (time.perf_counter() - t)
+        out[name] = {"iters_per_s": ips, "iters": its // reps,
+                     "frac_of_hbm": per_iter[name] * ips / 1e9 / hbm}
     return out
 
 

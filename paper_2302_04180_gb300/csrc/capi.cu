@@ -681,7 +681,9 @@ int rbs_solve_ex(const rbs_csr *A, const double *b, const double *x0, const doub
                                                                        smode & SPMV_MODE_MASK))
                    : a.vec;
         if (p_vec_grid.load() > 0) a.vec.grid = a.p3.grid = (int)p_vec_grid.load();
-        const int sb = block_of(p_spmv_block.load(), 256);
+        // long rows: the register-staged kernels' own block (the knob is for short rows)
+        const int sb = (smode & SPMV_MODE_MASK) == SPMV_MODE_LONG ? SPMV_REG_WARPS * 32
+                                                                  : block_of(p_spmv_block.load(), 256);
         a.spmv = grid_for(w, n, sb, solver_blocks_per_sm(variant, o.dot_mode, 0, sb, carve, smode & SPMV_MODE_MASK));
         a.spmv.mode = smode;
         a.k3 = variant == RBS_CLASSIC

@@ -384,7 +384,7 @@ __device__ __forceinline__ unsigned char *warp_scratch() {
     return buf + (threadIdx.x >> 5) * BYTES;
 }
 
-template <int Q, int SCRATCH = FLUSH_SCRATCH>
+template <int Q, int SCRATCH = FLUSH_SCRATCH, int WARPS = MAX_WARPS>
 __device__ __forceinline__ void warp_flush(Win<Q> &W, unsigned long long *sacc) {
     static_assert(SCRATCH >= FLUSH_SCRATCH, "flush staging");
     const unsigned FULL = 0xffffffffu;
@@ -398,8 +398,8 @@ __device__ __forceinline__ void warp_flush(Win<Q> &W, unsigned long long *sacc) 
         return;
     }
     __syncwarp();
-    long long(*st)[8] = reinterpret_cast<long long(*)[8]>(warp_scratch<SCRATCH>());  // 2 KB
-    int *off = reinterpret_cast<int *>(warp_scratch<SCRATCH>() + 32 * 8 * 8);        // 128 B
+    long long(*st)[8] = reinterpret_cast<long long(*)[8]>(warp_scratch<SCRATCH, WARPS>());  // 2 KB
+    int *off = reinterpret_cast<int *>(warp_scratch<SCRATCH, WARPS>() + 32 * 8 * 8);        // 128 B
 #pragma unroll
     for (int k = 0; k < 7; k++) st[lane][k] = has ? (long long)W.w[k] : 0ll;
     st[lane][7] = has ? (long long)(int32_t)W.w[7] : 0ll;
@@ -574,11 +574,13 @@ __device__ __forceinline__ bool block_grid_finish(const uint32_t (&flags)[K], un
 
 // Grid-level finish of K exact reductions held in register windows: flush the
 // windows into the block accumulators, then block_grid_finish (nblk: blocks
-// that share the reduction, 0 for the whole grid).
+// that share the reduction, 0 for the whole grid). SCRATCH, WARPS: the
+// per-warp shared buffer the kernel already uses (warp_scratch), which the
+// flush reuses.
 // coop = false: flush every lane's window with its own atomics, without the
 // warp's shared scratch (whose bytes a timed-out asynchronous copy may still
 // overwrite).
-template <int K, int Q, int SCRATCH = FLUSH_SCRATCH>
+template <int K, int Q, int SCRATCH = FLUSH_SCRATCH, int WARPS = MAX_WARPS>
 __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)[K],
                                              unsigned long long (*sacc)[NL], uint32_t *sflags,
                                              DotScratch *g, double *vals, bool export_limbs = false,
@@ -586,7 +588,7 @@ __device__ __forceinline__ bool exact_finish(Win<Q> (&win)[K], uint32_t (&flags)
                                              unsigned nblk = 0u, bool coop = true) {
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        if (coop) warp_flush<Q, SCRATCH>(win[k], sacc[k]);
+        if (coop) warp_flush<Q, SCRATCH, WARPS>(win[k], sacc[k]);
         else win_flush<Q>(win[k], sacc[k]);
     }
     return block_grid_finish<K>(flags, sacc, sflags, g, vals, export_limbs, limbs_out, flags_out, nblk);

@@ -380,8 +380,7 @@ stalled:
 // staged, are computed as in spmv_rows before the refill. Staging, the bounded
 // waits, the index checks and the timeout fallback are those of spmv_rows; the
 // arithmetic is exactly spmv_row's.
-constexpr int SPMV_REG_LEN = 28;
-constexpr int SPMV_REG_WARPS = 4;  // warps per block of the kernels using spmv_rows_reg
+constexpr int SPMV_REG_LEN = 28;  // (SPMV_REG_WARPS, the warps per block of its kernels: launch.h)
 template <bool CHECKED, int CAP, bool L2X, class F>
 __device__ __forceinline__ void spmv_rows_reg(const CSRView &A, int64_t r_begin, int64_t r_end, int64_t warp,
                                               int64_t nwarps, const double *__restrict__ x,

@@ -45,20 +45,44 @@ __global__ void __launch_bounds__(256) k_cls_setup(Ctx c) {
     if (red.finish(c.g, vals) && threadIdx.x == 0) tail_cls_setup(c.st, vals);
 }
 
+// SpMV rows of the fused K1/K3 with epilogue fn(row, y_row, z_row): short
+// rows warp-staged (or one thread per row, mode 1) in 256-thread blocks; long
+// rows (CAP = SPMV_CAP_LONG) register-staged in blocks of SPMV_REG_WARPS warps.
+// Finish the kernel's reducer with finish<FusedScratch<CAP>::BYTES,
+// FusedScratch<CAP>::WARPS>, so that its flush reuses the staging buffer.
+template <int CAP>
+struct FusedScratch {
+    static constexpr bool REG = CAP > SPMV_CAP_SHORT;
+    static constexpr int BYTES = REG ? SpmvLayout<CAP>::BUF : SpmvLayout<CAP>::SCRATCH;
+    static constexpr int WARPS = REG ? SPMV_REG_WARPS : MAX_WARPS;
+    static constexpr int THREADS = WARPS * 32;
+};
+template <int CAP, class F>
+__device__ __forceinline__ void fused_spmv(const Ctx &c, const double *x, const double *z, unsigned &eb, F &&fn) {
+    if (FusedScratch<CAP>::REG)
+        spmv_rows_reg<false, CAP, false>(c.A, 0, c.A.n, (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+                                         (int64_t)gridDim.x * (blockDim.x >> 5), x, z, true,
+                                         (c.spmv_mode & SPMV_TEST_STALL) != 0, eb, fn);
+    else
+        spmv_each<false, CAP>(c.A, x, z, c.spmv_mode, eb, fn);
+}
+
 // K1: s = A phat, <r0, s>
 template <class R, int CAP>
-__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k1(Ctx c) {
+__global__ void __launch_bounds__(FusedScratch<CAP>::THREADS, 3) k_cls_k1(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     unsigned eb = 0u;
-    spmv_each<false, CAP>(c.A, c.ph, c.r0, c.spmv_mode, eb, [&](int64_t i, double si, double r0) {
+    fused_spmv<CAP>(c, c.ph, c.r0, eb, [&](int64_t i, double si, double r0) {
         c.s[i] = si;
         red.add(0, r0, si);
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals, 0u, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0)
+    if (red.template finish<FusedScratch<CAP>::BYTES, FusedScratch<CAP>::WARPS>(c.g, vals, 0u,
+                                                                               !(eb & ERR_TIMEOUT)) &&
+        threadIdx.x == 0)
         tail_cls_alpha(c.st, vals);
 }
 
@@ -84,19 +108,21 @@ __global__ void __launch_bounds__(256, 4) k_cls_k2(Ctx c) {
 
 // K3: y = A qhat, <q, y>, <y, y>
 template <class R, int CAP>
-__global__ void __launch_bounds__(256, CAP > SPMV_CAP_SHORT ? 1 : 3) k_cls_k3(Ctx c) {
+__global__ void __launch_bounds__(FusedScratch<CAP>::THREADS, 3) k_cls_k3(Ctx c) {
     if (c.st->done) return;
     R red;
     red.init();
     unsigned eb = 0u;
-    spmv_each<false, CAP>(c.A, c.qh, c.q, c.spmv_mode, eb, [&](int64_t i, double yi, double qi) {
+    fused_spmv<CAP>(c, c.qh, c.q, eb, [&](int64_t i, double yi, double qi) {
         c.y[i] = yi;
         red.add(0, qi, yi);
         red.add_sq(1, yi);
     });
     if (eb) atomicOr(c.err, eb);
     __shared__ double vals[R::K];
-    if (red.template finish<SpmvLayout<CAP>::SCRATCH>(c.g, vals, 0u, !(eb & ERR_TIMEOUT)) && threadIdx.x == 0)
+    if (red.template finish<FusedScratch<CAP>::BYTES, FusedScratch<CAP>::WARPS>(c.g, vals, 0u,
+                                                                               !(eb & ERR_TIMEOUT)) &&
+        threadIdx.x == 0)
         tail_cls_omega(c.st, vals);
 }
 

@@ -24,6 +24,9 @@ struct CSRArgs {
 // Bit SPMV_TEST_STALL above the schedule bits selects the staged SpMV's test
 // mode of its bounded wait (kernels.cuh).
 enum : int { SPMV_MODE_ROW = 1, SPMV_MODE_SHORT = 2, SPMV_MODE_LONG = 3, SPMV_MODE_MASK = 0xff, SPMV_TEST_STALL = 0x100 };
+// Long rows run register-staged in blocks of SPMV_REG_WARPS warps: the
+// standalone SpMV, and the classic loop's fused K1/K3.
+constexpr int SPMV_REG_WARPS = 4;
 
 struct Cfg {
     int grid = 0;

@@ -41,9 +41,10 @@ struct ExactR {
     // SCRATCH: the per-warp scratch size the kernel already uses, so that the
     // flush staging shares it.
     // coop = false after a timed-out staged copy (ERR_TIMEOUT): per-lane flushes
-    template <int SCRATCH = FLUSH_SCRATCH>
+    template <int SCRATCH = FLUSH_SCRATCH, int WARPS = MAX_WARPS>
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u, bool coop = true) {
-        return exact_finish<K, Q, SCRATCH>(win, flags, sacc, sflags, g, vals, false, nullptr, nullptr, nblk, coop);
+        return exact_finish<K, Q, SCRATCH, WARPS>(win, flags, sacc, sflags, g, vals, false, nullptr, nullptr, nblk,
+                                                  coop);
     }
 };
 
@@ -226,7 +227,7 @@ struct PlainR {
     }
     __device__ __forceinline__ void add(int k, double x, double y) { s[k] = fma(x, y, s[k]); }
     __device__ __forceinline__ void add_sq(int k, double x) { s[k] = fma(x, x, s[k]); }
-    template <int SCRATCH = 0>
+    template <int SCRATCH = 0, int WARPS = MAX_WARPS>
     __device__ __forceinline__ bool finish(DotScratch *g, double *vals, unsigned nblk = 0u, bool coop = true) {
         (void)coop;  // its partials live in their own shared array
         __shared__ double s_part[K][32];

@@ -101,6 +101,54 @@ def test_stencil27_ragged_chunks(rbs, dev, orc, side):
     rbs.rbs_set_param("spmv.mode", 0)
 
 
+def _lengthen_rows(A, every, extra):
+    """A copy of A in which every `every`-th row gets `extra` more entries:
+    repeats of its own first entries (duplicates sum in stored order)."""
+    rows, cols, vals = [0], [], []
+    for i in range(A.n):
+        b, e = int(A.rowptr[i]), int(A.rowptr[i + 1])
+        c, v = list(A.col[b:e]), list(A.val[b:e])
+        if i % every == 0 and e > b:
+            c += [c[k % len(c)] for k in range(extra)]
+            v += [v[k % len(v)] * 0.5 for k in range(extra)]
+        cols += c
+        vals += v
+        rows.append(len(cols))
+    return gen.CSR(A.n, np.array(rows, np.int64), np.array(cols, np.int32), np.array(vals, np.float64))
+
+
+def test_long_rows_past_the_register_length(rbs, dev, orc):
+    """Chunks of the long-row schedule holding rows of more than 28 nonzeros
+    (every 37th row of a 27-point matrix lengthened to 35) are computed
+    from the staged buffer before it is refilled; the others from registers."""
+    A = _lengthen_rows(gen.stencil27(15), 37, 8)
+    x = gen.random_vector(A.n, 15)
+    ref = orc.spmv(A, x)
+    for mode in (0, 3):
+        rbs.rbs_set_param("spmv.mode", mode)
+        assert same_array(_spmv(rbs, dev, A, x), ref), mode
+    rbs.rbs_set_param("spmv.mode", 0)
+
+
+def test_long_rows_unaligned_arrays(rbs, dev, orc):
+    """col and val views 4 and 8 bytes past a 16-byte boundary: no bulk
+    copies; every chunk is staged by per-lane element copies."""
+    import torch
+    A = gen.stencil27(17)
+    colb = torch.zeros(A.nnz + 1, dtype=torch.int32, device=dev)
+    valb = torch.zeros(A.nnz + 1, dtype=torch.float64, device=dev)
+    colb[1:] = torch.from_numpy(A.col.astype(np.int32)).to(dev)
+    valb[1:] = torch.from_numpy(A.val).to(dev)
+    Ad = rbs.DeviceCSR(A.n, torch.from_numpy(A.rowptr.astype(np.int64)).to(dev), colb[1:], valb[1:])
+    assert Ad.col.data_ptr() % 16 == 4 and Ad.val.data_ptr() % 16 == 8
+    x = gen.random_vector(A.n, 17)
+    ref = orc.spmv(A, x)
+    for mode in (0, 2, 3):
+        rbs.rbs_set_param("spmv.mode", mode)
+        assert same_array(rbs.rbs_spmv_csr(Ad, torch.from_numpy(x).to(dev)).cpu().numpy(), ref), mode
+    rbs.rbs_set_param("spmv.mode", 0)
+
+
 def test_stencil27_159_full_size(rbs, dev, orc):
     """The 27-point e-type matrix at the benchmark's size (n = 4,019,679,
     nnz = 107,171,875), every row bitwise the oracle's."""
