@@ -17,7 +17,8 @@ struct DotArgs {
 };
 
 // K exact dots over the same length (Sec. 2 exdot; Sec. 4.1/4.2 merged
-// reductions). Aligned operands go through 16-byte loads, two pairs deep.
+// reductions). Aligned operands go through 16-byte loads, two pairs deep (long
+// dots of one or two outputs: the next two pairs in flight while these add).
 // SMEM: one or two outputs keep their windows in shared memory (ExactS: fewer
 // integer operations per product, dearer to clear and flush per thread); long
 // dots take it, short ones and more outputs keep register windows (ExactR2).
@@ -30,7 +31,67 @@ __global__ void __launch_bounds__(256) k_exdot(DotArgs<K> a, int64_t n, bool ali
                                               double *out, long long *limbs, int32_t *flags_out) {
     ExdotRed<K, Q, SMEM> red;
     red.init();
-    if (aligned) {
+    if (aligned && SMEM && K <= 2) {
+        // long dots (shared-memory windows): the next iteration's four pairs
+        // load while this one's are added, so that the stream does not stop
+        // for the products (2^27: 427 -> 400 us; the register-window reducer
+        // of shorter dots measured slower this way and keeps the loop below)
+        const int64_t n2 = n >> 1, st = gstride();
+        int64_t j = gtid();
+        if (j + st < n2) {
+            double2 xa[K], ya[K], xb[K], yb[K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                xa[k] = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + j);
+                ya[k] = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + j);
+                xb[k] = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + j + st);
+                yb[k] = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + j + st);
+            }
+            for (;;) {
+                const int64_t jn = j + 2 * st;
+                const bool more = jn + st < n2;
+                double2 xc[K], yc[K], xd[K], yd[K];
+                if (more) {
+#pragma unroll
+                    for (int k = 0; k < K; k++) {
+                        xc[k] = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + jn);
+                        yc[k] = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + jn);
+                        xd[k] = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + jn + st);
+                        yd[k] = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + jn + st);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    red.add(k, xa[k].x, ya[k].x);
+                    red.add(k, xa[k].y, ya[k].y);
+                    red.add(k, xb[k].x, yb[k].x);
+                    red.add(k, xb[k].y, yb[k].y);
+                }
+                j = jn;
+                if (!more) break;
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    xa[k] = xc[k];
+                    ya[k] = yc[k];
+                    xb[k] = xd[k];
+                    yb[k] = yd[k];
+                }
+            }
+        }
+        if (j < n2) {
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const double2 xv = __ldcs(reinterpret_cast<const double2 *>(a.x[k]) + j);
+                const double2 yv = __ldcs(reinterpret_cast<const double2 *>(a.y[k]) + j);
+                red.add(k, xv.x, yv.x);
+                red.add(k, xv.y, yv.y);
+            }
+        }
+        if ((n & 1) && gtid() == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k++) red.add(k, a.x[k][n - 1], a.y[k][n - 1]);
+        }
+    } else if (aligned) {
         const int64_t n2 = n >> 1, st = gstride();
         int64_t j = gtid();
         for (; j + st < n2; j += 2 * st) {
