@@ -799,6 +799,39 @@ def _trace_buckets(traces, width=25):
     return out
 
 
+def run_batched_only(args):
+    """Only the batched solve (C4): `--systems` of the seeded 512-system
+    workload under a given schedule (cluster:split; 0:0 is the stepped
+    schedule with rows per block chosen per chunk), one warm-up and `--steps`
+    timed calls; the profiling target of the batch kernels."""
+    import torch
+    import paper_2302_04180_gb300 as rbs
+    from paper_2302_04180_gb300 import gen
+    dev = torch.device("cuda:0")
+    cl, sp = (int(t) for t in args.schedule.split(":"))
+    work = gen.batch_workload(512, seed=0)[: args.systems]
+    systems = []
+    for A, v in work:
+        Ad = rbs.to_device(A, dev)
+        b = rbs.rbs_spmv_csr(Ad, torch.ones(A.n, dtype=torch.float64, device=dev))
+        systems.append({"A": Ad, "b": b, "x": torch.empty(A.n, dtype=torch.float64, device=dev),
+                        "tol": 1e-8, "maxit": 5000, "variant": v})
+    for _ in range(max(args.warmup, 1)):
+        res = rbs.rbs_solve_batched(systems, history=False, schedule={"cluster": cl, "split": sp})
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        res = rbs.rbs_solve_batched(systems, history=False, schedule={"cluster": cl, "split": sp})
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / max(args.steps, 1)
+    alg = sum(r["iters"] * (24 * A.nnz + (352 if v else 216) * A.n) for r, (A, v) in zip(res, work))
+    hbm, _ = _peaks()
+    print(json.dumps({"section": "batched", "systems": len(systems), "schedule": args.schedule, "seconds": dt,
+                      "total_iters": int(sum(r["iters"] for r in res)),
+                      "frac_of_hbm": alg / dt / 1e9 / hbm}), flush=True)
+    return 0
+
+
 def run_micro_spmv(args):
     """Standalone CSR SpMV on the named matrices (poisson:SIDE, the 7-point
     Poisson matrix; stencil27:SIDE, the 27-point e-type one), one JSON line per
@@ -895,6 +928,10 @@ def main():
     ap.add_argument("--micro-spmv", default=None, metavar="KIND:SIDE[,...]",
                     help="only the standalone SpMV microbenchmark on these matrices "
                          "(e.g. stencil27:159 or poisson:128); the profiling target of the SpMV")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched solve (C4) under --schedule; the profiling target of the batch kernels")
+    ap.add_argument("--systems", type=int, default=512, help="with --batched-only: systems of the workload")
+    ap.add_argument("--schedule", default="0:0", help="with --batched-only: cluster:split")
     args = ap.parse_args()
     global GRID
     GRID = args.grid
@@ -906,6 +943,8 @@ def main():
         return run_micro_exdot(args)
     if args.micro_spmv:
         return run_micro_spmv(args)
+    if args.batched_only:
+        return run_batched_only(args)
     if args.solve_only:
         return run_solve_only(args)
     return run_gpu(args)

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256, 3) k_step_cls_k3(const Ctx *ctxs, const S
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_step_cls_k4(const Ctx *ctxs, const StepTask *tasks) {
+__global__ void __launch_bounds__(256, 4) k_step_cls_k4(const Ctx *ctxs, const StepTask *tasks) {
     const StepTask t = tasks[blockIdx.x];
     const Ctx c = ctxs[t.sys];
     if (c.st->done) return;
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256, 3) k_step_spmv(const Ctx *ctxs, const Ste
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_step_pipe_p1(const Ctx *ctxs, const StepTask *tasks) {
+__global__ void __launch_bounds__(256, 3) k_step_pipe_p1(const Ctx *ctxs, const StepTask *tasks) {
     const StepTask t = tasks[blockIdx.x];
     const Ctx c = ctxs[t.sys];
     if (c.st->done) return;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) k_step_pipe_p1(const Ctx *ctxs, const Ste
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_step_pipe_p3(const Ctx *ctxs, const StepTask *tasks) {
+__global__ void __launch_bounds__(256, 2) k_step_pipe_p3(const Ctx *ctxs, const StepTask *tasks) {
     const StepTask t = tasks[blockIdx.x];
     const Ctx c = ctxs[t.sys];
     if (c.st->done) return;

@@ -22,12 +22,11 @@ REGS_PER_SM = 65536
 BLOCK = 256
 
 
-@pytest.fixture(scope="module")
-def report(tmp_path_factory):
+def _ptxas_report(tmp_path_factory, source):
     if shutil.which("nvcc") is None and not __import__("os").path.exists("/usr/local/cuda/bin/nvcc"):
         pytest.skip("nvcc not available")
-    obj = tmp_path_factory.mktemp("ptxas") / "kernels_solver.o"
-    cmd = [B.nvcc(), "-Xptxas=-v", *B.ARCH, *B.NVCC_FLAGS, "-c", f"{B.CSRC}/kernels_solver.cu", "-o", str(obj)]
+    obj = tmp_path_factory.mktemp("ptxas") / source.replace(".cu", ".o")
+    cmd = [B.nvcc(), "-Xptxas=-v", *B.ARCH, *B.NVCC_FLAGS, "-c", f"{B.CSRC}/{source}", "-o", str(obj)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
     out, name, spill = {}, None, 0
@@ -43,6 +42,16 @@ def report(tmp_path_factory):
             out[name] = (int(m.group(1)), spill)
             name = None
     return out
+
+
+@pytest.fixture(scope="module")
+def report(tmp_path_factory):
+    return _ptxas_report(tmp_path_factory, "kernels_solver.cu")
+
+
+@pytest.fixture(scope="module")
+def step_report(tmp_path_factory):
+    return _ptxas_report(tmp_path_factory, "kernels_step.cu")
 
 
 def _find(report, *parts):
@@ -84,3 +93,16 @@ def test_chosen_pipelined_shapes(report):
 def test_streaming_kernels_do_not_spill(report):
     for parts in (("k_cls_k2",), ("k_cls_k5",), ("k_cls_k4", EXACT), ("k_cls_k4", PLAIN)):
         assert _find(report, *parts)[1] == 0, parts
+
+
+def test_step_kernels_as_resident_as_the_solve_kernels(step_report):
+    """The per-step kernels (batched solves and the serving engine) run the
+    same element steps with per-system task indexing on top; left free, the
+    five-dot P3 took 138 registers and fitted one block per SM. They keep the
+    solve kernels' residency: P3 two blocks, P1 three, K4 four."""
+    assert _blocks(_find(step_report, "k_step_pipe_p3")[0]) >= 2
+    assert _blocks(_find(step_report, "k_step_pipe_p1")[0]) >= 3
+    regs, spill = _find(step_report, "k_step_cls_k4")
+    assert _blocks(regs) >= 4 and spill == 0
+    assert _blocks(_find(step_report, "k_step_cls_k1")[0]) >= 3
+    assert _blocks(_find(step_report, "k_step_cls_k3")[0]) >= 3
