@@ -7,9 +7,10 @@ device memory. Its only scratch is an 8 KiB array inside the library.
 
 The test calls it through the C ABI twice in a row (the shared array keeps the
 previous call's contents, which the entry point must clear) and checks every
-result against the existing rbs_exdot_multi entry point. Exact dots are
-compared bit for bit, the tolerance all exact-dot tests here use. This file is
-named to be collected last; it also passes alone in a fresh process.
+result against the existing rbs_exdot_multi entry point, the CPU oracle and
+the exact value the generator knows. Exact dots are compared bit for bit, the
+tolerance all exact-dot tests here use. This file is named to be collected
+last; it also passes alone in a fresh process.
 """
 import ctypes as C
 
@@ -22,7 +23,7 @@ from paper_2302_04180_gb300 import gen
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_exdot_multi_two_calls_in_a_row():
+def test_noalloc_matches_exdot_multi_two_calls_in_a_row(orc):
     import torch
     dev = cuda_device()
     import paper_2302_04180_gb300 as rbs
@@ -30,10 +31,11 @@ def test_noalloc_matches_exdot_multi_two_calls_in_a_row():
     f = lib.rbs_exdot_noalloc
     stream = torch.cuda.current_stream(dev).cuda_stream
     for call, (n, cond, k) in enumerate([(300007, 1e32, 3), (1 << 20, 1e48, 6)]):
-        vs = []
+        vs, refs = [], []
         for j in range(k):
-            x, y, _ = gen.ill_conditioned_dot(n, cond, seed=10 * call + j)
+            x, y, exact = gen.ill_conditioned_dot(n, cond, seed=10 * call + j)
             vs.append((torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)))
+            refs.append((orc.exdot(x, y), exact))
         xa = (C.c_void_p * k)(*[v[0].data_ptr() for v in vs])
         ya = (C.c_void_p * k)(*[v[1].data_ptr() for v in vs])
         out = torch.full((k,), float("nan"), dtype=torch.float64, device=dev)
@@ -44,6 +46,9 @@ def test_noalloc_matches_exdot_multi_two_calls_in_a_row():
         got, want = out.cpu().numpy(), ref.cpu().numpy()
         for j in range(k):
             assert same(got[j], want[j]), (call, j, got[j], want[j])
+            assert same(got[j], refs[j][0]), (call, j, got[j], refs[j][0])
+            if refs[j][1] is not None:
+                assert same(got[j], float(refs[j][1])), (call, j)
 
 
 def test_noalloc_rejects_more_dots_than_its_scratch_holds():
