@@ -67,3 +67,24 @@ def test_gpu_e_type_and_banded_parity(orc, variant):
                 assert same_array(g["x"].cpu().numpy(), o["x"])
     finally:
         rbs.rbs_set_param("spmv.mode", 0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("variant", [0, 1])
+def test_gpu_e_type_63_whole_history(orc, variant):
+    """The 27-point e-type matrix at 63^3 (n = 250,047: 7,814 chunks of 32 rows
+    and a tail of 31; edge rows of 8 to 18 nonzeros among interior rows of 27)
+    through the long-row kernels -- the fused K1/K3 of the classic loop, the
+    pipelined loop's SpMV -- to tol 1e-10: every history record, the iteration
+    count and x bitwise the oracle's."""
+    import torch
+    dev = cuda_device()
+    import paper_2302_04180_gb300 as rbs
+    A = gen.stencil27(63)
+    Ad = rbs.to_device(A, dev)
+    b = orc.spmv(A, np.ones(A.n))
+    o = orc.solve(A, b, tol=1e-10, maxit=800, variant=variant)
+    g = rbs.rbs_solve(Ad, torch.from_numpy(b).to(dev), tol=1e-10, maxit=800, variant=variant)
+    assert g["iters"] == o["iters"] > 50 and g["status"] == o["status"] == 0
+    assert same_array(g["hist"], o["hist"])
+    assert same_array(g["x"].cpu().numpy(), o["x"])
