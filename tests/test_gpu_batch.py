@@ -175,3 +175,37 @@ def test_batch_graph_replay_sees_new_data(dev):
             sd["b"].copy_(torch.from_numpy(gen.random_vector(n, 100 * rnd + k, lo=-1.0, hi=1.0)))
         res = rbs.rbs_solve_batched(systems)
         _same_as(res, _ref_solves(rbs, systems, work, 1500))
+
+
+@pytest.fixture(scope="module")
+def large_batch(orc):
+    """Three systems of 195k-287k unknowns (classic and pipelined; one stops at
+    its iteration cap of 400) with their oracle solves (the oracle threaded,
+    which is bitwise its one-thread result)."""
+    import os
+    work = gen.batch_workload(3, seed=21, n_min=100000, n_max=300000)
+    keep = orc.get_threads()
+    orc.set_threads(min(16, os.cpu_count() or 1))
+    try:
+        out = []
+        for A, variant in work:
+            b = orc.spmv(A, np.ones(A.n))
+            out.append((A, variant, b, orc.solve(A, b, tol=1e-8, maxit=400, variant=variant)))
+    finally:
+        orc.set_threads(keep)
+    assert sorted({v for _, v, _, _ in out}) == [0, 1]
+    assert any(o["converged"] == 0 for *_, o in out) and any(o["converged"] == 1 for *_, o in out)
+    return out
+
+
+@pytest.mark.parametrize("schedule", [None, {"cluster": 8, "split": 150000}, {"cluster": 0, "split": 0}])
+def test_batch_large_systems_match_oracle(dev, large_batch, schedule):
+    """Large systems under the persistent default (every CTA alone), the
+    persistent schedule with a cluster per system above the split, and the
+    stepped schedule: every history, iteration count and x bitwise the
+    oracle's."""
+    import paper_2302_04180_gb300 as rbs
+    systems = [_device_system(rbs, dev, A, v, 1e-8, 400, b=b) for A, v, b, _ in large_batch]
+    res = rbs.rbs_solve_batched(systems, schedule=schedule)
+    for g, (*_, o) in zip(res, large_batch):
+        _check(g, o)
