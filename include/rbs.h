@@ -368,8 +368,10 @@ int rbs_stream_status(void *stream);
 int rbs_release(void);
 /* Launch-shape knobs for tuning and for configuration-independence tests.
  * Names: "exdot.grid", "exdot.block", "exdot.window" (0 = auto),
- * "spmv.block", "spmv.mode" (0 auto: warp-staged rows, long-span staging when rows
- * average more than 8 nonzeros; 1 one thread per row; 2 short; 3 long staging),
+ * "spmv.block" (short rows; long rows run in their own 4-warp blocks),
+ * "spmv.mode" (0 auto: warp-staged rows, the long-row schedule when rows average
+ * more than 8 nonzeros -- one staging buffer per warp, each row's values and x
+ * entries moved to registers; 1 one thread per row; 2 short; 3 long rows),
  * "vec.grid", "vec.block", "solve.check_every", "smem.carveout" (percent of
  * L1/shared storage for the staging kernels; default 75, -1 = driver default);
  * "test.stall_staging" (1: a test mode of the bounded device-side wait --
