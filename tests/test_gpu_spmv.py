@@ -86,6 +86,30 @@ def test_bad_column_is_reported_not_read(rbs, dev, mode):
         rbs.rbs_set_param("spmv.mode", 0)
 
 
+@pytest.mark.parametrize("long_rows", [False, True])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_malformed_row_pointers_are_reported(rbs, dev, mode, long_rows):
+    """A row pointer that runs backwards, or past nnz, is caught by the kernel's
+    own checks under every schedule (the chunk is not staged and the row is
+    skipped), reported as RBS_EINVAL; the next call is clean."""
+    import torch
+    A = gen.stencil27(9) if long_rows else gen.poisson3d(10)
+    for bad_value in (int(A.rowptr[A.n // 2 + 1]) + 5, A.nnz + 1000):
+        rp = A.rowptr.copy()
+        rp[A.n // 2] = bad_value
+        bad = gen.CSR(A.n, rp, A.col, A.val)
+        Bd = rbs.to_device(bad, dev)
+        try:
+            rbs.rbs_set_param("spmv.mode", mode)
+            rbs.rbs_spmv_csr(Bd, torch.ones(A.n, dtype=torch.float64, device=dev))
+            with pytest.raises(rbs.RbsError) as e:
+                rbs.rbs_stream_status()
+            assert e.value.code == rbs.RBS_EINVAL
+            rbs.rbs_stream_status()  # cleared
+        finally:
+            rbs.rbs_set_param("spmv.mode", 0)
+
+
 @pytest.mark.parametrize("side", [7, 21, 33])
 def test_stencil27_ragged_chunks(rbs, dev, orc, side):
     """Long rows (27 nonzeros) through the register-staged schedule: n = 343,
