@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librbs.so")
-SOURCES = ["kernels_dot.cu", "kernels_solver.cu", "kernels_step.cu", "kernels_batch.cu", "capi.cu", "server.cu"]
+SOURCES = ["kernels_dot.cu", "kernels_exdot_w1.cu", "kernels_exdot_w2.cu", "kernels_spmv.cu", "kernels_solver.cu",
+           "kernels_step.cu", "kernels_batch.cu", "capi.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fno-fast-math", "-Xcompiler", "-ffp-contract=off",

@@ -51,6 +51,15 @@ cudaError_t launch_fpe_dot(const double *x, const double *y, int64_t n, DotScrat
 // block size, for dots of length n (the kernel variant depends on it): the
 // persistent grid is a whole number of waves of it.
 int exdot_blocks_per_sm(int k, int window, int block, int64_t n);
+// The same kernels with 1- and 2-limb register windows (kernels_exdot_w1.cu,
+// kernels_exdot_w2.cu): launch and resident blocks per SM (smem: the
+// shared-memory-window reducer of long one- and two-output dots).
+cudaError_t launch_exdot_w1(int k, const double *const *xs, const double *const *ys, int64_t n, DotScratch *g,
+                            double *out, Cfg cfg, cudaStream_t s);
+cudaError_t launch_exdot_w2(int k, const double *const *xs, const double *const *ys, int64_t n, DotScratch *g,
+                            double *out, Cfg cfg, cudaStream_t s);
+int exdot_occ_w1(int k, int block, bool smem);
+int exdot_occ_w2(int k, int block, bool smem);
 int fpe_blocks_per_sm(int block);
 cudaError_t launch_round_limbs(const int64_t *limbs, const int32_t *flags, double *out, cudaStream_t s);
 // y = A x. Without a solver state every index is checked (ERR_INDEX on a bad

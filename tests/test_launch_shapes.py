@@ -106,3 +106,27 @@ def test_step_kernels_as_resident_as_the_solve_kernels(step_report):
     assert _blocks(regs) >= 4 and spill == 0
     assert _blocks(_find(step_report, "k_step_cls_k1")[0]) >= 3
     assert _blocks(_find(step_report, "k_step_cls_k3")[0]) >= 3
+
+
+@pytest.fixture(scope="module")
+def dot_report(tmp_path_factory):
+    return _ptxas_report(tmp_path_factory, "kernels_spmv.cu")
+
+
+def _blocks_of(regs, threads):
+    per_warp = ((regs + 7) // 8) * 8 * 32
+    return REGS_PER_SM // (per_warp * (threads // 32))
+
+
+def test_long_row_kernels_fit_three_four_warp_blocks(dot_report, report):
+    """The register-staged long-row SpMV holds each row's values and x entries
+    in registers and relies on three 128-thread blocks per SM (12 warps) to keep
+    a chain of fmas ready on every SM sub-partition: at most 168 registers, and
+    the standalone kernel without spills. The fused classic K1/K3 on long rows
+    keep the same residency."""
+    for name in ("k_spmv_regILb0", "k_spmv_regILb1"):
+        regs, spill = _find(dot_report, name)
+        assert _blocks_of(regs, 128) >= 3 and spill == 0, (name, regs, spill)
+    for kern, red in (("k_cls_k1", "ExactRILi1"), ("k_cls_k3", "ExactRILi2")):
+        regs, _ = _find(report, kern, red, "Li1024E")
+        assert _blocks_of(regs, 128) >= 3, (kern, regs)
