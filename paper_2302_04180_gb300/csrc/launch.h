@@ -40,7 +40,8 @@ int set_error(int code, const char *msg);
 // Free the workspace of stream `s` on the current device (before the stream is destroyed).
 void release_stream_workspace(cudaStream_t s);
 
-// ---- standalone kernels (kernels_dot.cu) ----
+// ---- standalone kernels (kernels_dot.cu: exact dots, limbs, FPE-8;
+// kernels_spmv.cu: SpMV, Jacobi, CSR check) ----
 cudaError_t launch_exdot(int k, const double *const *xs, const double *const *ys, int64_t n,
                          DotScratch *g, double *out, int window, Cfg cfg, cudaStream_t s);
 cudaError_t launch_exdot_partial(const double *x, const double *y, int64_t n, DotScratch *g,
